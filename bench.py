@@ -1,0 +1,404 @@
+"""Benchmark: primary rays/s of the batched exact ray cast on one GB300.
+
+One step = one whole pass of the hot path over one batch: a 64 x 64 crater
+edit with incremental pyramid repair, then one batched render of the 64
+cameras of the batched-cameras workload (16 x 3840x2160, 24 x 1920x1080,
+24 x 640x360, half top-down, half eye level) with one shadow ray per hit, on
+the 2048 x 2048 walls-and-caves grid.  value = primary rays / s over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hf|reference]
+                  [--workload c3|c2|c4|c1]
+
+Under torchrun each rank renders its own copy of the batch (weak scaling, no
+data-path collective); rank 0 prints one JSON line.
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HBM_FALLBACK = 6800.0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ workloads
+
+def workload(name, rank=0):
+    import synth
+
+    if name == "c3":
+        cfg = synth.config_c3()
+        return dict(name="C3 batched cameras: 2048x2048 walls+caves grid (seed 2), 64 cameras "
+                         "(16x3840x2160, 24x1920x1080, 24x640x360), shadow rays on, one 64x64 "
+                         "crater edit + incremental pyramid repair per step",
+                    cells=cfg["cells"], cams=cfg["cams"], shadows=True, edit=True)
+    if name == "c2":
+        cfg = synth.config_c2()
+        return dict(name="C2 eye-level horizon: 2048x2048 walls+caves grid, one 1920x1080 camera "
+                         "2 units above the floor, pitch 0, hfov 90",
+                    cells=cfg["cells"], cams=cfg["cams"], shadows=False, edit=False)
+    if name == "c1":
+        cfg = synth.config_c1()
+        return dict(name="C1 small: 256x256 grid, one 320x240 camera", cells=cfg["cells"],
+                    cams=cfg["cams"], shadows=False, edit=False)
+    if name == "c4":
+        cells = synth.config_c4()["cells"]
+        return dict(name="C4 large world: 2048x16384 grid (seed 4, 30% slabs), 1000-frame "
+                         "1920x1080 fly-through; one step = 100 frames in one batch",
+                    cells=cells, cams=synth.config_c4_frames(cells, 1000), shadows=False,
+                    edit=False, frames_per_step=100)
+    raise SystemExit("unknown workload " + name)
+
+
+def n_rays(cams):
+    return int(sum(int(c["w"]) * int(c["h"]) for c in cams))
+
+
+# -------------------------------------------------------------- clocks probe
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# --------------------------------------------------------------- CPU oracle
+
+def cpu_oracle_sample(wl, budget_s=15.0, seed=0):
+    """Oracle rays/s on a bounded, seeded sample of the workload's pixels."""
+    import oracle
+
+    cores = os.cpu_count() or 1
+    cams = wl["cams"]
+    rng = np.random.default_rng(seed)
+    per = 64
+    t0 = time.perf_counter()
+    done = 0
+    rounds = 0
+    while time.perf_counter() - t0 < budget_s and rounds < 64:
+        for c in cams:
+            n = int(c["w"]) * int(c["h"])
+            pix = np.sort(rng.integers(0, n, per)).astype(np.uint32)
+            oracle.render(wl["cells"], c, shadows=wl["shadows"], pix=pix, nthreads=cores)
+            done += per
+        rounds += 1
+        per = min(per * 2, 4096)
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "primary rays/s", "cores": cores, "kind": "oracle",
+            "sample": "%d seeded pixels spread over all %d cameras of the workload%s, %.1f s"
+                      % (done, len(cams), " with shadow rays" if wl["shadows"] else "", dt)}
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_hf(args):
+    import torch
+
+    import __graft_entry__
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0 or ws > 1:
+        __graft_entry__.build_library()
+    import paper_2608_17390_gb300 as hf
+    import synth
+
+    wl = workload(args.workload, rank)
+    cells = wl["cells"].copy()
+    cams_all = wl["cams"]
+    fps = wl.get("frames_per_step")
+    stream = torch.cuda.Stream()
+    ctx = hf.hf_create(cells, stream=stream.cuda_stream)
+    info = hf.hf_info(ctx)
+    flags = hf.HF_SHADOWS if wl["shadows"] else 0
+    opts = hf.make_opts(flags=flags, mip_start=args.mip, tile_w=args.tile_w, tile_h=args.tile_h)
+
+    def step_cams(i):
+        if fps:
+            k = (i * fps) % len(cams_all)
+            return cams_all[k:k + fps]
+        return cams_all
+
+    max_cams = step_cams(0)
+    outs = hf.alloc_outputs(max_cams, device="cuda", shadows=wl["shadows"])
+    rng = np.random.default_rng(1234 + rank)
+    H, W = cells.shape
+
+    def do_edit():
+        cx, cy = int(rng.integers(0, W)), int(rng.integers(0, H))
+        x0, y0, blk = synth.crater_edit(cells, cx, cy)
+        hf.hf_edit(ctx, x0, y0, blk)
+        cells[y0:y0 + blk.shape[0], x0:x0 + blk.shape[1]] = blk
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+
+    def one_step(i, rec=None):
+        cams = step_cams(i)
+        if rec:
+            rec[0].record(stream)
+        if wl["edit"]:
+            do_edit()
+        if rec:
+            rec[1].record(stream)
+        hf.hf_render(ctx, cams, outs[:len(cams)], opts)
+        if rec:
+            rec[2].record(stream)
+
+    # untimed: fetch counters for the algorithmic bytes of one render
+    sopts = hf.make_opts(flags=flags | hf.HF_STATS, mip_start=args.mip, tile_w=args.tile_w,
+                         tile_h=args.tile_h)
+    hf.hf_stats(ctx)
+    hf.hf_render(ctx, max_cams, outs[:len(max_cams)], sopts)
+    st = hf.hf_stats(ctx)
+    for i in range(args.warmup):
+        one_step(i)
+    hf.hf_sync(ctx)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(torch.cuda.current_device())
+    if rank == 0:
+        clocks.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    render_ms, step_ms = [], []
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xFF)  # evict L2 between timed steps (256 MiB > L2)
+        one_step(args.warmup + i, ev[i])
+    hf.hf_sync(ctx)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    ck = clocks.stop() if rank == 0 else None
+    for a, b, c in ev:
+        step_ms.append(a.elapsed_time(c))
+        render_ms.append(b.elapsed_time(c))
+    total_ms = float(np.sum(step_ms))
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    rays_step = sum(n_rays(step_cams(args.warmup + i)) for i in range(args.steps)) / args.steps
+    value = rays_step * args.steps * ws / (total_ms / 1e3)
+
+    # plain: one launch per camera, same accuracy, same stream, L2 flushed
+    plain = None
+    if not args.no_plain:
+        popts = hf.make_opts(flags=flags | hf.HF_PLAIN, mip_start=args.mip, tile_w=args.tile_w,
+                             tile_h=args.tile_h)
+        pms = []
+        for i in range(max(1, min(3, args.steps))):
+            with torch.cuda.stream(stream):
+                flush.fill_(7)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            hf.hf_render(ctx, max_cams, outs[:len(max_cams)], popts)
+            b.record(stream)
+            hf.hf_sync(ctx)
+            pms.append(a.elapsed_time(b))
+        plain = n_rays(max_cams) / (float(np.median(pms)) / 1e3)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host = [{k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in o.items()}
+                for o in outs[:len(max_cams)]]
+        cam_bytes = max_cams.nbytes
+        out_bytes = sum(v.numel() * v.element_size() for o in host for v in o.values())
+        ems = []
+        for i in range(max(1, min(3, args.steps))):
+            with torch.cuda.stream(stream):
+                flush.fill_(9)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if wl["edit"]:
+                do_edit()
+            hf.hf_render(ctx, max_cams, outs[:len(max_cams)], opts)
+            with torch.cuda.stream(stream):
+                for o, h in zip(outs, host):
+                    for k in o:
+                        h[k].copy_(o[k], non_blocking=True)
+            stream.synchronize()
+            ems.append(time.perf_counter() - t0)
+        e2e = {"value": n_rays(max_cams) / float(np.median(ems)), "unit": "primary rays/s",
+               "h2d_bytes_per_step": int(cam_bytes + (64 * 64 * 4 if wl["edit"] else 0)),
+               "d2h_bytes_per_step": int(out_bytes)}
+
+    hf.hf_destroy(ctx)
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    hbm, src = _peaks()
+    rays = st["rays"]
+    out_b = rays * (14 + (1 if wl["shadows"] else 0))
+    fetch_b = 4 * (st["node_fetches"] + st["cell_fetches"] + st["shadow_fetches"])
+    alg_bytes = fetch_b + out_b
+    r_ms = float(np.mean(render_ms))
+    achieved = alg_bytes / (r_ms / 1e3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic_%s.json" % args.workload)
+    if os.path.exists(tfile):
+        try:
+            traffic = json.load(open(tfile)).get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    line = {
+        "metric": "primary rays/s (batched, exact two-interval height-field ray cast)",
+        "value": value, "unit": "primary rays/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+        "data": "synthetic (seeded value-noise terrain standing in for the paper's Fostral level)",
+        "config": {"workload": wl["name"], "rays_per_step": int(rays_step),
+                   "grid": "%dx%d" % (W, H), "l2": "flushed between steps (256 MiB write)",
+                   "mip_start": "auto" if args.mip == 0xFFFFFFFF else args.mip,
+                   "tile": "%dx%d" % (args.tile_w or 8, args.tile_h or 4),
+                   "world_bytes": info["cell_bytes"] + info["pyramid_bytes"]},
+        "plain_rays_per_s": plain,
+        "batched_over_plain": (value / ws / plain) if plain else None,
+        "render_ms": r_ms,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic,
+                     "peak_source": src,
+                     "bytes_per_ray": alg_bytes / max(rays, 1),
+                     "note": "algorithmic bytes = 4 B x (pyramid nodes + cells + shadow-ray "
+                             "fetches, counted in-kernel) + %d B output per ray; most fetches "
+                             "are L2/L1 hits" % (14 + (1 if wl["shadows"] else 0))},
+        "fetches_per_ray": (st["node_fetches"] + st["cell_fetches"]) / max(rays, 1),
+        "gpu_launches": args.steps * ((2 if wl["edit"] else 1)),
+        "clocks": ck,
+        "e2e": e2e,
+    }
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_sample(wl, budget_s=args.cpu_seconds)
+    print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    wl = workload(args.workload)
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_oracle_sample(wl, budget_s=per_step)
+    vals = []
+    last = None
+    for i in range(args.steps):
+        last = cpu_oracle_sample(wl, budget_s=per_step, seed=i + 1)
+        vals.append(last["value"])
+    value = float(np.median(vals))
+    line = {"impl": "reference", "metric": "primary rays/s (batched, exact two-interval "
+            "height-field ray cast)", "value": value, "unit": "primary rays/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i64",
+            "data": "synthetic", "config": {"workload": wl["name"]},
+            "cpu_baseline": dict(last, value=value),
+            "e2e": {"value": value, "unit": "primary rays/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hf", choices=["hf", "reference"])
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4"])
+    ap.add_argument("--mip", type=int, default=0xFFFFFFFF)
+    ap.add_argument("--tile-w", type=int, default=0)
+    ap.add_argument("--tile-h", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "hf":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_hf(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * hf.h -- C ABI of an exact two-interval height-field ray caster (GB300, sm_103a).
+ *
+ * The operation (arxiv 2608.17390, Malyshau, "Six Ways to Draw Vangers with
+ * WebGPU"): each ground cell holds two solid intervals, a floor [.., h0] and an
+ * optional slab [h1, h2] (Section 2, The Data); a point is solid when
+ * z <= h0 or h1 <= z <= h2 (the SOLID predicate of Section 3.1, closed ends,
+ * no lower bound on the floor); one ray is cast per pixel and the first solid
+ * point along it is reported; a bounded rectangular edit must be visible on the
+ * next render without a rebuild (Sections 2 and 4.4).  The library answers
+ * this exactly with fixed-point integer arithmetic, skipping empty space with a
+ * conservative min/max pyramid (the "skip only known-empty space" rule of the
+ * hierarchy in Section 3.2) that an edit repairs incrementally.
+ *
+ * Units.  One world unit is one cell width and one height step.  Positions are
+ * fixed point in units of 2^-16 world units.  A pixel ray is p(t) = O + t d,
+ * t >= 0, with integer O and d.
+ *
+ * Cell word (uint32, little-endian bytes): byte0 h0, byte1 h1, byte2 h2,
+ * byte3 material.  A cell has a slab iff h1 > h0, and then h2 >= h1; a cell
+ * without a slab must store h1 = h2 = 0.  Other combinations are rejected.
+ *
+ * Result of a ray.  The ray visits the cells whose (half-open) column it
+ * occupies for a positive length of t; each visit covers a closed interval of
+ * t.  The hit is the first visited cell, in visit order, whose closed interval
+ * holds a solid t, at the smallest such t; the ray misses when it leaves the
+ * grid first.  At an exact cell corner the ray steps diagonally; the entry
+ * face is then the X face.
+ *
+ * Errors.  Every function returns an int: HF_OK (0) or a negative HF_E_* code.
+ * No C++ exception crosses this interface.  A context is not thread-safe: use
+ * one context per host thread or lock around calls.
+ */
+#ifndef HF_H
+#define HF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+#define HF_OK 0
+#define HF_E_INVALID_ARG (-1)   /* null pointer, zero or oversize extent, invalid cell, bad camera */
+#define HF_E_OUT_OF_BOUNDS (-2) /* edit/read rectangle outside the grid */
+#define HF_E_OOM (-3)           /* device or pinned host allocation failed */
+#define HF_E_CUDA (-4)          /* a CUDA runtime call failed */
+#define HF_E_STEP_LIMIT (-5)    /* a ray exceeded its traversal step guard (its face = HF_FACE_ERROR) */
+#define HF_E_BUSY (-6)          /* every render slot is in flight (only with HF_NOWAIT) */
+
+/* face codes written to hf_outputs.face */
+#define HF_FACE_NX 0     /* entered through its -X side (ray moving +x) */
+#define HF_FACE_PX 1     /* entered through its +X side (ray moving -x) */
+#define HF_FACE_NY 2     /* entered through its -Y side (ray moving +y) */
+#define HF_FACE_PY 3     /* entered through its +Y side (ray moving -y) */
+#define HF_FACE_NZ 4     /* slab underside (cave ceiling), ray moving up */
+#define HF_FACE_PZ 5     /* top of the floor or of the slab, ray moving down */
+#define HF_FACE_INSIDE 6 /* the ray starts inside solid (t = 0) */
+#define HF_FACE_ERROR 254
+#define HF_FACE_MISS 255
+
+/* hf_render_opts.flags */
+#define HF_SHADOWS 1u /* trace one shadow ray per hit toward the sun */
+#define HF_PLAIN 2u   /* one non-persistent launch per camera instead of one batched launch */
+#define HF_SYNC 4u    /* wait for the render and return its status (HF_E_STEP_LIMIT) */
+#define HF_STATS 8u   /* count node and cell fetches (read back with hf_stats) */
+#define HF_NOGRAPH 16u /* launch directly instead of replaying a captured CUDA graph */
+#define HF_NOWAIT 32u /* return HF_E_BUSY instead of waiting for a free render slot */
+
+#define HF_MIP_AUTO 0xFFFFFFFFu
+
+#define HF_MAX_DIM 16384u     /* largest grid width/height and image width/height */
+#define HF_MAX_CAMERAS 4096u  /* largest batch in one hf_render call */
+
+/* --------------------------------------------------------------- types */
+typedef struct hf_ctx hf_ctx; /* opaque: owns the device grid, pyramid and scratch */
+
+typedef struct {
+    uint32_t width, height; /* grid size in cells, 1..HF_MAX_DIM each */
+    const uint32_t *cells;  /* HOST pointer to height rows of row_stride cell words */
+    size_t row_stride;      /* cells per row in `cells`; 0 means width */
+    void *cuda_stream;      /* cudaStream_t all work of this context is ordered on;
+                               NULL: the library creates (and destroys) its own */
+} hf_desc;
+
+/* Integer camera.  Pixel (px, py), py = 0 at the top row, looks along
+ *   d = fwd + (2 px + 1 - w) right + (h - 1 - 2 py) up.
+ * Valid when 0 <= origin[0] < W*65536, 0 <= origin[1] < H*65536,
+ * 0 <= origin[2] < 2^28, 1 <= w, h <= HF_MAX_DIM, and |fwd_i|, |right_i|*(w-1),
+ * |up_i|*(h-1) and every corner pixel's |d_i| are each below 2^21. */
+typedef struct {
+    int64_t origin[3]; /* 2^-16 world units */
+    int32_t fwd[3], right[3], up[3];
+    uint32_t w, h;
+} hf_camera;
+
+/* Per-camera DEVICE output buffers, each w*h elements in row-major pixel
+ * order (py*w + px).  Caller-owned; they must stay allocated until the render
+ * has completed on the context's stream.  A NULL member is not written. */
+typedef struct {
+    uint32_t *hit_cell; /* y*W + x of the hit cell; 0xFFFFFFFF on a miss */
+    uint8_t *layer;     /* 0 floor, 1 slab, 255 miss */
+    uint8_t *face;      /* HF_FACE_* */
+    float *depth;       /* t*|d|/65536 world units (Euclidean); +inf on a miss */
+    uint32_t *rgba;     /* shaded colour, bytes r,g,b,a */
+    uint8_t *shadow;    /* 1 when the sun is occluded (written only with HF_SHADOWS) */
+} hf_outputs;
+
+typedef struct {
+    uint32_t tile_w, tile_h; /* pixels per warp tile (powers of two, product 32..128);
+                                0,0 = default 8 x 4 */
+    uint32_t mip_start;      /* coarsest pyramid level the traversal uses and starts at;
+                                0 = flat cell-by-cell DDA; HF_MIP_AUTO = library default;
+                                larger values are clamped to the pyramid's top level */
+    uint32_t flags;          /* HF_SHADOWS | HF_PLAIN | HF_SYNC | HF_STATS | HF_NOGRAPH | HF_NOWAIT */
+    uint32_t max_steps;      /* traversal iterations allowed per ray; 0 = default guard */
+    int32_t sun[3];          /* direction toward the sun; all zero = (321060, -321060, 262144),
+                                elevation 30 deg, azimuth 135 deg; each |sun_i| < 2^21 */
+    void *cuda_stream;       /* stream for this render; NULL = the context's stream */
+} hf_render_opts;
+
+typedef struct {
+    uint32_t width, height, levels; /* grid size; pyramid levels above the cells */
+    uint32_t render_slots;          /* concurrent renders the context can hold in flight */
+    uint64_t cell_bytes;            /* device bytes of the cell grid */
+    uint64_t pyramid_bytes;         /* device bytes of the pyramid (levels 1..levels) */
+    uint64_t scratch_bytes;         /* device bytes of per-render scratch (camera tables) */
+    int32_t device;                 /* CUDA device ordinal */
+    int32_t sm_count;
+} hf_info_t;
+
+/* ------------------------------------------------------------ functions */
+
+/* Create a context: validates every cell (Section 2 two-interval encoding),
+ * copies the grid to the device, builds the pyramid (levels 1..ceil(log2
+ * max(W,H))).  The caller may free desc->cells when this returns.  The device
+ * is the current CUDA device.  On error *out is set to NULL.
+ * Errors: HF_E_INVALID_ARG (null, bad size, invalid cell), HF_E_OOM, HF_E_CUDA. */
+int hf_create(const hf_desc *desc, hf_ctx **out);
+
+/* Overwrite the cells of rectangle [x0, x0+w) x [y0, y0+h) with `cells` (HOST
+ * pointer, h rows of row_stride cells; 0 = w) and repair the pyramid nodes that
+ * cover it, level by level (the incremental rebuild of affected cells and their
+ * ancestors, Sections 2 and 3.2).  The cells are staged before return, so the
+ * caller may reuse its buffer at once.  The edit is ordered on the context's
+ * stream after every render issued before it (renders issued on other streams
+ * included) and before every render issued after it: those renders see it,
+ * earlier ones do not (the first-frame visibility of Section 4.4).
+ * w = 0 or h = 0 is a no-op.  Errors: HF_E_INVALID_ARG (null, invalid cell),
+ * HF_E_OUT_OF_BOUNDS (rectangle outside the grid), HF_E_OOM, HF_E_CUDA. */
+int hf_edit(hf_ctx *ctx, uint32_t x0, uint32_t y0, uint32_t w, uint32_t h,
+            const uint32_t *cells, size_t row_stride);
+
+/* Render n cameras (HOST array) into outs[0..n-1] (HOST array of structs that
+ * hold DEVICE pointers).  Asynchronous on the render stream unless HF_SYNC.
+ * opts = NULL uses the defaults.  n = 0 is a no-op.
+ * Errors: HF_E_INVALID_ARG (null, n > HF_MAX_CAMERAS, invalid camera or tile
+ * shape), HF_E_BUSY (HF_NOWAIT and no free slot), HF_E_CUDA, and with HF_SYNC
+ * HF_E_STEP_LIMIT when a ray hit its step guard. */
+int hf_render(hf_ctx *ctx, const hf_camera *cams, uint32_t n, const hf_outputs *outs,
+              const hf_render_opts *opts);
+
+/* Wait for all work the context issued (every render slot and the context
+ * stream).  Returns HF_E_STEP_LIMIT if any ray of any render since the last
+ * hf_sync hit its step guard (and clears that flag), else HF_OK / HF_E_CUDA. */
+int hf_sync(hf_ctx *ctx);
+
+/* Synchronise, then free every device and host resource of the context.
+ * NULL is accepted.  Returns HF_OK or HF_E_CUDA. */
+int hf_destroy(hf_ctx *ctx);
+
+/* Host helper: quantise a pose into an integer camera, in float64.  yaw 0
+ * looks along +y, yaw 90 along +x; pitch < 0 looks down; hfov is the
+ * horizontal field of view with square pixels.  The focal length is fixed in
+ * pixels, f = (w/2)/tan(hfov/2), independent of h (Section 4.1 records a
+ * reference camera whose focal length scaled with the image height).
+ * fwd = rnd(2^19 forward), right = rnd(2^18/f right), up = rnd(2^18/f up),
+ * origin = rnd(2^16 (x, y, z)), rnd rounding half away from zero.
+ * Errors: HF_E_INVALID_ARG (null out, w or h outside 1..HF_MAX_DIM,
+ * hfov outside (0, 180)). */
+int hf_camera_from_pose(double x, double y, double z, double yaw_deg, double pitch_deg,
+                        double hfov_deg, uint32_t w, uint32_t h, hf_camera *out);
+
+/* Host check of one camera against a W x H grid (the range limits above).
+ * Returns HF_OK or HF_E_INVALID_ARG. */
+int hf_validate_camera(uint32_t grid_w, uint32_t grid_h, const hf_camera *cam);
+
+/* Host check of n cell words (the two-interval encoding above).
+ * Returns HF_OK or HF_E_INVALID_ARG; *bad_index (may be NULL) gets the first bad word. */
+int hf_validate_cells(const uint32_t *cells, size_t n, size_t *bad_index);
+
+/* Static text for a code (never NULL). */
+const char *hf_strerror(int code);
+
+/* Sizes and device of a context.  Errors: HF_E_INVALID_ARG. */
+int hf_info(const hf_ctx *ctx, hf_info_t *out);
+
+/* Copy cells of a rectangle back to HOST memory (synchronous).
+ * Errors: HF_E_INVALID_ARG, HF_E_OUT_OF_BOUNDS, HF_E_CUDA. */
+int hf_read_cells(hf_ctx *ctx, uint32_t x0, uint32_t y0, uint32_t w, uint32_t h,
+                  uint32_t *out, size_t row_stride);
+
+/* Copy pyramid level `level` (1..levels) to HOST memory (synchronous):
+ * ceil(H/2^level) rows of ceil(W/2^level) node words, byte0 max h0, byte1 min
+ * over cells of (slab ? h1 : 255), byte2 max over cells of (slab ? h2 : h0).
+ * Errors: HF_E_INVALID_ARG, HF_E_CUDA. */
+int hf_read_pyramid(hf_ctx *ctx, uint32_t level, uint32_t *out);
+
+/* Rebuild the whole pyramid from the cells (the same kernels a full-grid edit
+ * runs).  Errors: HF_E_INVALID_ARG, HF_E_CUDA. */
+int hf_rebuild(hf_ctx *ctx);
+
+/* Synchronise and read the fetch counters accumulated by HF_STATS renders:
+ * out[0] pyramid node fetches, out[1] cell fetches, out[2] primary rays,
+ * out[3] shadow rays, out[4] fetches made by shadow rays.  Clears them.
+ * Errors: HF_E_INVALID_ARG, HF_E_CUDA. */
+int hf_stats(hf_ctx *ctx, uint64_t out[5]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HF_H */

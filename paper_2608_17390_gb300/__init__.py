@@ -1,0 +1,290 @@
+"""Python binding of libhf.so: exact two-interval height-field ray casting on GB300.
+
+A thin ctypes layer over the C ABI in include/hf.h, with the same names:
+``hf_create``, ``hf_edit``, ``hf_render``, ``hf_sync``, ``hf_destroy``,
+``hf_camera_from_pose``, ``hf_validate_camera``, ``hf_validate_cells``,
+``hf_strerror``, ``hf_info``, ``hf_read_cells``, ``hf_read_pyramid``,
+``hf_rebuild``, ``hf_stats``.  It only marshals arguments: every step of the
+ray cast runs in the library's CUDA kernels.  PyTorch provides device memory
+(output tensors) and streams.
+
+Importing this module loads libhf.so and raises if it is missing (build it
+with ``python -c "import __graft_entry__ as g; g.build()"``); there is no CPU
+fallback.  Errors from the library raise ``HFError``.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhf.so")
+
+HF_OK = 0
+HF_E_INVALID_ARG = -1
+HF_E_OUT_OF_BOUNDS = -2
+HF_E_OOM = -3
+HF_E_CUDA = -4
+HF_E_STEP_LIMIT = -5
+HF_E_BUSY = -6
+
+HF_FACE_NX, HF_FACE_PX, HF_FACE_NY, HF_FACE_PY, HF_FACE_NZ, HF_FACE_PZ, HF_FACE_INSIDE = range(7)
+HF_FACE_ERROR = 254
+HF_FACE_MISS = 255
+
+HF_SHADOWS = 1
+HF_PLAIN = 2
+HF_SYNC = 4
+HF_STATS = 8
+HF_NOGRAPH = 16
+HF_NOWAIT = 32
+HF_MIP_AUTO = 0xFFFFFFFF
+HF_MAX_DIM = 16384
+HF_MAX_CAMERAS = 4096
+
+
+class HFError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (where, hf_strerror(code), code))
+
+
+class hf_desc(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_uint32), ("height", ctypes.c_uint32),
+                ("cells", ctypes.c_void_p), ("row_stride", ctypes.c_size_t),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class hf_camera(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_int64 * 3), ("fwd", ctypes.c_int32 * 3),
+                ("right", ctypes.c_int32 * 3), ("up", ctypes.c_int32 * 3),
+                ("w", ctypes.c_uint32), ("h", ctypes.c_uint32)]
+
+
+class hf_outputs(ctypes.Structure):
+    _fields_ = [("hit_cell", ctypes.c_void_p), ("layer", ctypes.c_void_p),
+                ("face", ctypes.c_void_p), ("depth", ctypes.c_void_p),
+                ("rgba", ctypes.c_void_p), ("shadow", ctypes.c_void_p)]
+
+
+class hf_render_opts(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_uint32), ("tile_h", ctypes.c_uint32),
+                ("mip_start", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("max_steps", ctypes.c_uint32), ("sun", ctypes.c_int32 * 3),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class hf_info_t(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_uint32), ("height", ctypes.c_uint32),
+                ("levels", ctypes.c_uint32), ("render_slots", ctypes.c_uint32),
+                ("cell_bytes", ctypes.c_uint64), ("pyramid_bytes", ctypes.c_uint64),
+                ("scratch_bytes", ctypes.c_uint64), ("device", ctypes.c_int32),
+                ("sm_count", ctypes.c_int32)]
+
+
+# numpy view of hf_camera (same layout as the C struct)
+CAMERA_DTYPE = np.dtype(
+    [("o", "<i8", (3,)), ("f", "<i4", (3,)), ("r", "<i4", (3,)),
+     ("u", "<i4", (3,)), ("w", "<u4"), ("h", "<u4")], align=True)
+assert CAMERA_DTYPE.itemsize == ctypes.sizeof(hf_camera)
+
+OUTPUT_FIELDS = ("hit_cell", "layer", "face", "depth", "rgba", "shadow")
+
+_P = ctypes.c_void_p
+_U32 = ctypes.c_uint32
+_SIGS = {
+    "hf_create": ([ctypes.POINTER(hf_desc), ctypes.POINTER(_P)], ctypes.c_int),
+    "hf_edit": ([_P, _U32, _U32, _U32, _U32, _P, ctypes.c_size_t], ctypes.c_int),
+    "hf_render": ([_P, _P, _U32, _P, ctypes.POINTER(hf_render_opts)], ctypes.c_int),
+    "hf_sync": ([_P], ctypes.c_int),
+    "hf_destroy": ([_P], ctypes.c_int),
+    "hf_camera_from_pose": ([ctypes.c_double] * 6 + [_U32, _U32, ctypes.POINTER(hf_camera)],
+                            ctypes.c_int),
+    "hf_validate_camera": ([_U32, _U32, ctypes.POINTER(hf_camera)], ctypes.c_int),
+    "hf_validate_cells": ([_P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "hf_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "hf_info": ([_P, ctypes.POINTER(hf_info_t)], ctypes.c_int),
+    "hf_read_cells": ([_P, _U32, _U32, _U32, _U32, _P, ctypes.c_size_t], ctypes.c_int),
+    "hf_read_pyramid": ([_P, _U32, _P], ctypes.c_int),
+    "hf_rebuild": ([_P], ctypes.c_int),
+    "hf_stats": ([_P, _P], ctypes.c_int),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libhf.so is not built (%s); run the package build first" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (args, res) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+lib = _load()
+
+
+def _check(rc, where):
+    if rc != HF_OK:
+        raise HFError(rc, where)
+
+
+def hf_strerror(code):
+    return lib.hf_strerror(int(code)).decode()
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+def hf_create(cells, stream=None):
+    """Create a context from a uint32 [H, W] host array of cell words.
+
+    stream: a cudaStream_t handle (int), or None for torch's current stream.
+    Returns the opaque context handle (int)."""
+    c = np.ascontiguousarray(cells, dtype=np.uint32)
+    if c.ndim != 2:
+        raise ValueError("cells must be a 2-D array")
+    H, W = c.shape
+    d = hf_desc(W, H, c.ctypes.data, W, stream if stream is not None else _current_stream())
+    h = _P()
+    _check(lib.hf_create(ctypes.byref(d), ctypes.byref(h)), "hf_create")
+    return h.value
+
+
+def hf_edit(ctx, x0, y0, block):
+    """Overwrite the cells of a rectangle at (x0, y0) with a uint32 [h, w] host array."""
+    b = np.ascontiguousarray(block, dtype=np.uint32)
+    h, w = b.shape
+    _check(lib.hf_edit(ctx, int(x0), int(y0), w, h, b.ctypes.data, w), "hf_edit")
+
+
+def camera_records(cams):
+    """A contiguous CAMERA_DTYPE array from records with fields o, f, r, u, w, h."""
+    a = np.asarray(cams)
+    if a.dtype != CAMERA_DTYPE:
+        out = np.zeros(a.shape, CAMERA_DTYPE)
+        for k in CAMERA_DTYPE.names:
+            out[k] = a[k]
+        a = out
+    return np.ascontiguousarray(a.reshape(-1))
+
+
+def _outputs_array(outs):
+    arr = (hf_outputs * len(outs))()
+    for i, o in enumerate(outs):
+        for k in OUTPUT_FIELDS:
+            t = o.get(k) if isinstance(o, dict) else getattr(o, k, None)
+            setattr(arr[i], k, None if t is None else int(t.data_ptr()))
+    return arr
+
+
+def make_opts(tile_w=0, tile_h=0, mip_start=HF_MIP_AUTO, flags=0, max_steps=0, sun=(0, 0, 0),
+              stream=None):
+    return hf_render_opts(tile_w, tile_h, mip_start, flags, max_steps,
+                          (ctypes.c_int32 * 3)(*sun), stream)
+
+
+def hf_render(ctx, cams, outs, opts=None):
+    """Render camera records into per-camera dicts of device tensors.
+
+    cams: CAMERA_DTYPE array (or records with the same fields); outs: a list
+    of dicts keyed by hit_cell, layer, face, depth, rgba, shadow (missing or
+    None entries are not written); opts: an hf_render_opts or None."""
+    recs = camera_records(cams)
+    n = len(recs)
+    if len(outs) != n:
+        raise ValueError("one output set per camera")
+    oarr = _outputs_array(outs)
+    popts = ctypes.byref(opts) if opts is not None else None
+    rc = lib.hf_render(ctx, recs.ctypes.data if n else None, n, oarr, popts)
+    _check(rc, "hf_render")
+
+
+def hf_sync(ctx):
+    _check(lib.hf_sync(ctx), "hf_sync")
+
+
+def hf_destroy(ctx):
+    _check(lib.hf_destroy(ctx), "hf_destroy")
+
+
+def hf_camera_from_pose(x, y, z, yaw_deg, pitch_deg, hfov_deg, w, h):
+    """Quantise a pose; returns one CAMERA_DTYPE record."""
+    c = hf_camera()
+    _check(lib.hf_camera_from_pose(x, y, z, yaw_deg, pitch_deg, hfov_deg, w, h, ctypes.byref(c)),
+           "hf_camera_from_pose")
+    rec = np.zeros(1, CAMERA_DTYPE)
+    ctypes.memmove(rec.ctypes.data, ctypes.byref(c), ctypes.sizeof(c))
+    return rec[0]
+
+
+def hf_validate_camera(grid_w, grid_h, cam):
+    rec = camera_records(np.asarray([cam]))
+    c = hf_camera.from_buffer_copy(rec.tobytes())
+    return lib.hf_validate_camera(grid_w, grid_h, ctypes.byref(c))
+
+
+def hf_validate_cells(cells):
+    """Returns (code, first_bad_index or None)."""
+    c = np.ascontiguousarray(cells, dtype=np.uint32).reshape(-1)
+    bad = ctypes.c_size_t(0)
+    rc = lib.hf_validate_cells(c.ctypes.data if c.size else None, c.size, ctypes.byref(bad))
+    return rc, (bad.value if rc != HF_OK else None)
+
+
+def hf_info(ctx):
+    i = hf_info_t()
+    _check(lib.hf_info(ctx, ctypes.byref(i)), "hf_info")
+    return {k: getattr(i, k) for k, _ in hf_info_t._fields_}
+
+
+def hf_read_cells(ctx, x0, y0, w, h):
+    out = np.empty((h, w), np.uint32)
+    _check(lib.hf_read_cells(ctx, x0, y0, w, h, out.ctypes.data, w), "hf_read_cells")
+    return out
+
+
+def hf_read_pyramid(ctx, level):
+    info = hf_info(ctx)
+    wk = (info["width"] + (1 << level) - 1) >> level
+    hk = (info["height"] + (1 << level) - 1) >> level
+    out = np.empty((hk, wk), np.uint32)
+    _check(lib.hf_read_pyramid(ctx, level, out.ctypes.data), "hf_read_pyramid")
+    return out
+
+
+def hf_rebuild(ctx):
+    _check(lib.hf_rebuild(ctx), "hf_rebuild")
+
+
+def hf_stats(ctx):
+    v = (ctypes.c_uint64 * 5)()
+    _check(lib.hf_stats(ctx, v), "hf_stats")
+    return dict(node_fetches=v[0], cell_fetches=v[1], rays=v[2], shadow_rays=v[3],
+                shadow_fetches=v[4])
+
+
+def alloc_outputs(cams, device="cuda", shadows=False, fields=OUTPUT_FIELDS):
+    """Allocate one dict of device tensors per camera (torch)."""
+    import torch
+    dt = dict(hit_cell=torch.int32, layer=torch.uint8, face=torch.uint8, depth=torch.float32,
+              rgba=torch.int32, shadow=torch.uint8)
+    outs = []
+    for c in camera_records(cams):
+        n = int(c["w"]) * int(c["h"])
+        o = {}
+        for k in fields:
+            if k == "shadow" and not shadows:
+                continue
+            o[k] = torch.empty(n, dtype=dt[k], device=device)
+        outs.append(o)
+    return outs

@@ -1,0 +1,641 @@
+// hf_api.cpp -- host side of the C ABI declared in include/hf.h.
+//
+// A context owns one device allocation holding the cells and every pyramid
+// level, a pinned staging buffer for edits, and a ring of render slots.  Each
+// slot has a pinned camera-table staging buffer, a device copy of it, an event
+// that marks the slot's last render as complete, and a small cache of CUDA
+// graphs (H2D copy of the camera table -> persistent trace kernel).
+//
+// Ordering rules (the edit-visibility rule of the paper's Section 4.4):
+//   * every edit runs on the context stream, after waiting for the events of
+//     all slots, so no in-flight render (on any stream) can observe it;
+//   * a render on a foreign stream first waits for the last edit's event.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "hf.h"
+#include "hf_internal.h"
+
+namespace {
+
+constexpr int kSlots = 8;
+constexpr size_t kScratchAlign = 4096;
+constexpr int kMaxGraphsPerSlot = 16;
+constexpr int32_t kLimit21 = 1 << 21;
+constexpr int32_t kDefaultSun[3] = {321060, -321060, 262144};
+constexpr uint32_t kDefaultMip = 5;
+
+struct GraphKey {
+    uint32_t bytes, shadows, stats, twl, thl, mip, steps;
+    int32_t sun[3];
+    bool operator==(const GraphKey &o) const { return std::memcmp(this, &o, sizeof(*this)) == 0; }
+};
+
+struct Slot {
+    void *d_scratch = nullptr;
+    void *h_staging = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;
+    bool pending = false;
+    std::vector<std::pair<GraphKey, cudaGraphExec_t>> graphs;
+};
+
+}  // namespace
+
+struct hf_ctx {
+    int device = 0;
+    int sm_count = 0;
+    uint32_t W = 0, H = 0, L = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    uint32_t *d_world = nullptr;
+    size_t world_words = 0;
+    hf::WorldDev wd{};
+    uint32_t *h_edit = nullptr;
+    size_t edit_cap = 0;
+    cudaEvent_t edit_copy_done = nullptr;
+    bool edit_pending = false;
+    cudaEvent_t edit_done = nullptr;
+    Slot slots[kSlots];
+    int next_slot = 0;
+    uint32_t *d_status = nullptr;
+    uint32_t *h_status = nullptr;
+    unsigned long long *d_stats = nullptr;
+    int occ[2][2] = {{0, 0}, {0, 0}};
+};
+
+#define CK(call)                                   \
+    do {                                           \
+        if ((call) != cudaSuccess) {               \
+            (void)cudaGetLastError();              \
+            return HF_E_CUDA;                      \
+        }                                          \
+    } while (0)
+
+namespace {
+
+bool cell_ok(uint32_t c) {
+    const uint32_t h0 = c & 0xFF, h1 = (c >> 8) & 0xFF, h2 = (c >> 16) & 0xFF;
+    if (h1 > h0) return h2 >= h1;
+    return h1 == 0 && h2 == 0;
+}
+
+int check_rows(const uint32_t *cells, uint32_t w, uint32_t h, size_t stride) {
+    for (uint32_t y = 0; y < h; ++y) {
+        const uint32_t *row = cells + (size_t)y * stride;
+        for (uint32_t x = 0; x < w; ++x)
+            if (!cell_ok(row[x])) return HF_E_INVALID_ARG;
+    }
+    return HF_OK;
+}
+
+int64_t iabs64(int64_t v) { return v < 0 ? -v : v; }
+
+double rnd(double v) { return std::copysign(std::floor(std::fabs(v) + 0.5), v); }
+
+uint32_t levels_for(uint32_t W, uint32_t H) {
+    const uint32_t m = W > H ? W : H;
+    uint32_t L = 0;
+    while ((1u << L) < m) ++L;
+    return L;
+}
+
+int ilog2_exact(uint32_t v) {
+    if (v == 0 || (v & (v - 1))) return -1;
+    int k = 0;
+    while ((1u << k) < v) ++k;
+    return k;
+}
+
+int sync_slots(hf_ctx *c) {
+    for (auto &s : c->slots) {
+        if (s.pending) {
+            CK(cudaEventSynchronize(s.done));
+            s.pending = false;
+        }
+    }
+    return HF_OK;
+}
+
+void free_graphs(Slot &s) {
+    for (auto &g : s.graphs) cudaGraphExecDestroy(g.second);
+    s.graphs.clear();
+}
+
+int read_status(hf_ctx *c) {
+    CK(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (*c->h_status) {
+        CK(cudaMemsetAsync(c->d_status, 0, sizeof(uint32_t), c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        return HF_E_STEP_LIMIT;
+    }
+    return HF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *hf_strerror(int code) {
+    switch (code) {
+        case HF_OK: return "ok";
+        case HF_E_INVALID_ARG: return "invalid argument";
+        case HF_E_OUT_OF_BOUNDS: return "rectangle outside the grid";
+        case HF_E_OOM: return "out of memory";
+        case HF_E_CUDA: return "CUDA runtime error";
+        case HF_E_STEP_LIMIT: return "a ray exceeded its traversal step guard";
+        case HF_E_BUSY: return "every render slot is in flight";
+        default: return "unknown error";
+    }
+}
+
+int hf_validate_cells(const uint32_t *cells, size_t n, size_t *bad_index) {
+    if (!cells && n) return HF_E_INVALID_ARG;
+    for (size_t i = 0; i < n; ++i) {
+        if (!cell_ok(cells[i])) {
+            if (bad_index) *bad_index = i;
+            return HF_E_INVALID_ARG;
+        }
+    }
+    return HF_OK;
+}
+
+int hf_validate_camera(uint32_t W, uint32_t H, const hf_camera *c) {
+    if (!c || W == 0 || H == 0 || W > HF_MAX_DIM || H > HF_MAX_DIM) return HF_E_INVALID_ARG;
+    if (c->w == 0 || c->h == 0 || c->w > HF_MAX_DIM || c->h > HF_MAX_DIM) return HF_E_INVALID_ARG;
+    if (c->origin[0] < 0 || c->origin[0] >= (int64_t)W << 16) return HF_E_INVALID_ARG;
+    if (c->origin[1] < 0 || c->origin[1] >= (int64_t)H << 16) return HF_E_INVALID_ARG;
+    if (c->origin[2] < 0 || c->origin[2] >= ((int64_t)1 << 28)) return HF_E_INVALID_ARG;
+    for (int i = 0; i < 3; ++i) {
+        if (iabs64(c->fwd[i]) >= kLimit21) return HF_E_INVALID_ARG;
+        if (iabs64(c->right[i]) * (int64_t)(c->w - 1) >= kLimit21) return HF_E_INVALID_ARG;
+        if (iabs64(c->up[i]) * (int64_t)(c->h - 1) >= kLimit21) return HF_E_INVALID_ARG;
+        for (int ca = 0; ca < 2; ++ca) {
+            for (int cb = 0; cb < 2; ++cb) {
+                const int64_t a = ca ? (int64_t)c->w - 1 : 1 - (int64_t)c->w;
+                const int64_t b = cb ? (int64_t)c->h - 1 : 1 - (int64_t)c->h;
+                const int64_t d = (int64_t)c->fwd[i] + a * c->right[i] + b * c->up[i];
+                if (iabs64(d) >= kLimit21) return HF_E_INVALID_ARG;
+            }
+        }
+    }
+    return HF_OK;
+}
+
+int hf_camera_from_pose(double x, double y, double z, double yaw_deg, double pitch_deg,
+                        double hfov_deg, uint32_t w, uint32_t h, hf_camera *out) {
+    if (!out || w == 0 || h == 0 || w > HF_MAX_DIM || h > HF_MAX_DIM) return HF_E_INVALID_ARG;
+    if (!(hfov_deg > 0.0 && hfov_deg < 180.0)) return HF_E_INVALID_ARG;
+    const double deg = M_PI / 180.0;
+    const double yaw = yaw_deg * deg, pitch = pitch_deg * deg;
+    const double sy = std::sin(yaw), cy = std::cos(yaw), sp = std::sin(pitch),
+                 cp = std::cos(pitch);
+    const double fwd[3] = {sy * cp, cy * cp, sp};
+    const double right[3] = {cy, -sy, 0.0};
+    const double up[3] = {-sy * sp, -cy * sp, cp};
+    const double f_px = (w / 2.0) / std::tan(hfov_deg * deg / 2.0);
+    const double scale = 262144.0 / f_px;
+    for (int i = 0; i < 3; ++i) {
+        out->fwd[i] = (int32_t)rnd(524288.0 * fwd[i]);
+        out->right[i] = (int32_t)rnd(scale * right[i]);
+        out->up[i] = (int32_t)rnd(scale * up[i]);
+    }
+    out->origin[0] = (int64_t)rnd(x * 65536);
+    out->origin[1] = (int64_t)rnd(y * 65536);
+    out->origin[2] = (int64_t)rnd(z * 65536);
+    out->w = w;
+    out->h = h;
+    return HF_OK;
+}
+
+int hf_destroy(hf_ctx *c) {
+    if (!c) return HF_OK;
+    int rc = HF_OK;
+    cudaSetDevice(c->device);
+    sync_slots(c);
+    if (c->stream && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = HF_E_CUDA;
+    for (auto &s : c->slots) {
+        free_graphs(s);
+        if (s.done) cudaEventDestroy(s.done);
+        if (s.d_scratch) cudaFree(s.d_scratch);
+        if (s.h_staging) cudaFreeHost(s.h_staging);
+    }
+    if (c->edit_copy_done) cudaEventDestroy(c->edit_copy_done);
+    if (c->edit_done) cudaEventDestroy(c->edit_done);
+    if (c->h_edit) cudaFreeHost(c->h_edit);
+    if (c->h_status) cudaFreeHost(c->h_status);
+    if (c->d_status) cudaFree(c->d_status);
+    if (c->d_stats) cudaFree(c->d_stats);
+    if (c->d_world) cudaFree(c->d_world);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    (void)cudaGetLastError();
+    delete c;
+    return rc;
+}
+
+static int create_impl(const hf_desc *d, hf_ctx *c) {
+    CK(cudaGetDevice(&c->device));
+    CK(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
+    c->W = d->width;
+    c->H = d->height;
+    c->L = levels_for(c->W, c->H);
+    if (d->cuda_stream) {
+        c->stream = (cudaStream_t)d->cuda_stream;
+    } else {
+        CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    // level layout: cells, then each pyramid level, 64-word (256 B) aligned
+    size_t off = 0;
+    for (uint32_t k = 0; k <= c->L; ++k) {
+        const uint32_t wk = (c->W + (1u << k) - 1) >> k, hk = (c->H + (1u << k) - 1) >> k;
+        c->wd.off[k] = (uint32_t)off;
+        c->wd.stride[k] = wk;
+        off += ((size_t)wk * hk + 63) & ~(size_t)63;
+    }
+    c->world_words = off;
+    c->wd.W = (int32_t)c->W;
+    c->wd.H = (int32_t)c->H;
+    c->wd.L = (int32_t)c->L;
+    if (cudaMalloc(&c->d_world, off * sizeof(uint32_t)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return HF_E_OOM;
+    }
+    c->wd.base = c->d_world;
+    const size_t stride = d->row_stride ? d->row_stride : d->width;
+    CK(cudaMemcpy2DAsync(c->d_world, (size_t)c->W * 4, d->cells, stride * 4, (size_t)c->W * 4,
+                         c->H, cudaMemcpyHostToDevice, c->stream));
+    if (hf::pyramid_repair(c->d_world, c->wd, 0, 0, (int32_t)c->W, (int32_t)c->H, c->stream))
+        return HF_E_CUDA;
+    if (cudaMalloc(&c->d_status, sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&c->d_stats, 5 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaHostAlloc(&c->h_status, sizeof(uint32_t), cudaHostAllocDefault) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return HF_E_OOM;
+    }
+    CK(cudaMemsetAsync(c->d_status, 0, sizeof(uint32_t), c->stream));
+    CK(cudaMemsetAsync(c->d_stats, 0, 5 * sizeof(unsigned long long), c->stream));
+    CK(cudaEventCreateWithFlags(&c->edit_copy_done, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->edit_done, cudaEventDisableTiming));
+    CK(cudaEventRecord(c->edit_done, c->stream));
+    for (auto &s : c->slots) CK(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
+    for (int sh = 0; sh < 2; ++sh)
+        for (int st = 0; st < 2; ++st)
+            if (hf::trace_batched_occupancy(sh, st, &c->occ[sh][st]) || c->occ[sh][st] < 1)
+                return HF_E_CUDA;
+    CK(cudaStreamSynchronize(c->stream));
+    return HF_OK;
+}
+
+int hf_create(const hf_desc *d, hf_ctx **out) {
+    if (!out) return HF_E_INVALID_ARG;
+    *out = nullptr;
+    if (!d || !d->cells || d->width == 0 || d->height == 0 || d->width > HF_MAX_DIM ||
+        d->height > HF_MAX_DIM)
+        return HF_E_INVALID_ARG;
+    const size_t stride = d->row_stride ? d->row_stride : d->width;
+    if (stride < d->width) return HF_E_INVALID_ARG;
+    if (check_rows(d->cells, d->width, d->height, stride) != HF_OK) return HF_E_INVALID_ARG;
+    hf_ctx *c = new (std::nothrow) hf_ctx();
+    if (!c) return HF_E_OOM;
+    const int rc = create_impl(d, c);
+    if (rc != HF_OK) {
+        hf_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return HF_OK;
+}
+
+int hf_info(const hf_ctx *c, hf_info_t *out) {
+    if (!c || !out) return HF_E_INVALID_ARG;
+    out->width = c->W;
+    out->height = c->H;
+    out->levels = c->L;
+    out->render_slots = kSlots;
+    out->cell_bytes = (uint64_t)c->W * c->H * 4;
+    out->pyramid_bytes = (uint64_t)(c->world_words - c->wd.off[c->L > 0 ? 1 : 0]) * 4;
+    if (c->L == 0) out->pyramid_bytes = 0;
+    uint64_t sb = 0;
+    for (const auto &s : c->slots) sb += s.cap;
+    out->scratch_bytes = sb;
+    out->device = c->device;
+    out->sm_count = c->sm_count;
+    return HF_OK;
+}
+
+int hf_edit(hf_ctx *c, uint32_t x0, uint32_t y0, uint32_t w, uint32_t h, const uint32_t *cells,
+            size_t row_stride) {
+    if (!c) return HF_E_INVALID_ARG;
+    if (w == 0 || h == 0) return HF_OK;
+    if (!cells) return HF_E_INVALID_ARG;
+    if ((uint64_t)x0 + w > c->W || (uint64_t)y0 + h > c->H) return HF_E_OUT_OF_BOUNDS;
+    const size_t stride = row_stride ? row_stride : w;
+    if (stride < w) return HF_E_INVALID_ARG;
+    if (check_rows(cells, w, h, stride) != HF_OK) return HF_E_INVALID_ARG;
+    CK(cudaSetDevice(c->device));
+    const size_t need = (size_t)w * h * sizeof(uint32_t);
+    if (c->edit_pending) {
+        CK(cudaEventSynchronize(c->edit_copy_done));
+        c->edit_pending = false;
+    }
+    if (need > c->edit_cap) {
+        if (c->h_edit) cudaFreeHost(c->h_edit);
+        c->h_edit = nullptr;
+        c->edit_cap = 0;
+        const size_t cap = (need + kScratchAlign - 1) & ~(kScratchAlign - 1);
+        if (cudaHostAlloc(&c->h_edit, cap, cudaHostAllocDefault) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return HF_E_OOM;
+        }
+        c->edit_cap = cap;
+    }
+    for (uint32_t y = 0; y < h; ++y)
+        std::memcpy(c->h_edit + (size_t)y * w, cells + (size_t)y * stride, (size_t)w * 4);
+    // no in-flight render may observe the edit
+    for (auto &s : c->slots)
+        if (s.pending) CK(cudaStreamWaitEvent(c->stream, s.done, 0));
+    CK(cudaMemcpy2DAsync(c->d_world + (size_t)y0 * c->W + x0, (size_t)c->W * 4, c->h_edit,
+                         (size_t)w * 4, (size_t)w * 4, h, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaEventRecord(c->edit_copy_done, c->stream));
+    c->edit_pending = true;
+    if (hf::pyramid_repair(c->d_world, c->wd, (int32_t)x0, (int32_t)y0, (int32_t)(x0 + w),
+                           (int32_t)(y0 + h), c->stream))
+        return HF_E_CUDA;
+    CK(cudaEventRecord(c->edit_done, c->stream));
+    return HF_OK;
+}
+
+int hf_rebuild(hf_ctx *c) {
+    if (!c) return HF_E_INVALID_ARG;
+    CK(cudaSetDevice(c->device));
+    for (auto &s : c->slots)
+        if (s.pending) CK(cudaStreamWaitEvent(c->stream, s.done, 0));
+    if (hf::pyramid_repair(c->d_world, c->wd, 0, 0, (int32_t)c->W, (int32_t)c->H, c->stream))
+        return HF_E_CUDA;
+    CK(cudaEventRecord(c->edit_done, c->stream));
+    return HF_OK;
+}
+
+int hf_sync(hf_ctx *c) {
+    if (!c) return HF_E_INVALID_ARG;
+    CK(cudaSetDevice(c->device));
+    if (sync_slots(c) != HF_OK) return HF_E_CUDA;
+    CK(cudaStreamSynchronize(c->stream));
+    return read_status(c);
+}
+
+int hf_read_cells(hf_ctx *c, uint32_t x0, uint32_t y0, uint32_t w, uint32_t h, uint32_t *out,
+                  size_t row_stride) {
+    if (!c || !out) return HF_E_INVALID_ARG;
+    if (w == 0 || h == 0) return HF_OK;
+    if ((uint64_t)x0 + w > c->W || (uint64_t)y0 + h > c->H) return HF_E_OUT_OF_BOUNDS;
+    const size_t stride = row_stride ? row_stride : w;
+    if (stride < w) return HF_E_INVALID_ARG;
+    CK(cudaSetDevice(c->device));
+    CK(cudaMemcpy2DAsync(out, stride * 4, c->d_world + (size_t)y0 * c->W + x0, (size_t)c->W * 4,
+                         (size_t)w * 4, h, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return HF_OK;
+}
+
+int hf_read_pyramid(hf_ctx *c, uint32_t level, uint32_t *out) {
+    if (!c || !out || level == 0 || level > c->L) return HF_E_INVALID_ARG;
+    CK(cudaSetDevice(c->device));
+    const size_t wk = c->wd.stride[level];
+    const size_t hk = (c->H + (1u << level) - 1) >> level;
+    CK(cudaMemcpyAsync(out, c->d_world + c->wd.off[level], wk * hk * 4, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return HF_OK;
+}
+
+int hf_stats(hf_ctx *c, uint64_t out[5]) {
+    if (!c || !out) return HF_E_INVALID_ARG;
+    CK(cudaSetDevice(c->device));
+    if (sync_slots(c) != HF_OK) return HF_E_CUDA;
+    unsigned long long v[5];
+    CK(cudaMemcpyAsync(v, c->d_stats, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemsetAsync(c->d_stats, 0, sizeof(v), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < 5; ++i) out[i] = v[i];
+    return HF_OK;
+}
+
+static int acquire_slot(hf_ctx *c, bool nowait, int *idx) {
+    for (int k = 0; k < kSlots; ++k) {
+        const int i = (c->next_slot + k) % kSlots;
+        Slot &s = c->slots[i];
+        if (!s.pending) {
+            *idx = i;
+            c->next_slot = (i + 1) % kSlots;
+            return HF_OK;
+        }
+        const cudaError_t q = cudaEventQuery(s.done);
+        if (q == cudaSuccess) {
+            s.pending = false;
+            *idx = i;
+            c->next_slot = (i + 1) % kSlots;
+            return HF_OK;
+        }
+        if (q != cudaErrorNotReady) {
+            (void)cudaGetLastError();
+            return HF_E_CUDA;
+        }
+    }
+    if (nowait) return HF_E_BUSY;
+    const int i = c->next_slot;
+    CK(cudaEventSynchronize(c->slots[i].done));
+    c->slots[i].pending = false;
+    *idx = i;
+    c->next_slot = (i + 1) % kSlots;
+    return HF_OK;
+}
+
+static int ensure_slot_cap(Slot &s, size_t bytes) {
+    if (bytes <= s.cap) return HF_OK;
+    free_graphs(s);
+    if (s.d_scratch) cudaFree(s.d_scratch);
+    if (s.h_staging) cudaFreeHost(s.h_staging);
+    s.d_scratch = nullptr;
+    s.h_staging = nullptr;
+    s.cap = 0;
+    if (cudaMalloc(&s.d_scratch, bytes) != cudaSuccess ||
+        cudaHostAlloc(&s.h_staging, bytes, cudaHostAllocDefault) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return HF_E_OOM;
+    }
+    s.cap = bytes;
+    return HF_OK;
+}
+
+static int launch_graph(hf_ctx *c, Slot &s, const GraphKey &key, const hf::RenderParams &p,
+                        bool shadows, bool stats, cudaStream_t stream) {
+    cudaGraphExec_t exec = nullptr;
+    for (auto &g : s.graphs)
+        if (g.first == key) exec = g.second;
+    if (!exec) {
+        cudaGraph_t graph;
+        CK(cudaGraphCreate(&graph, 0));
+        cudaGraphNode_t copy, kern;
+        if (cudaGraphAddMemcpyNode1D(&copy, graph, nullptr, 0, s.d_scratch, s.h_staging, key.bytes,
+                                     cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            return HF_E_CUDA;
+        }
+        hf::RenderParams pc = p;
+        void *args[] = {&pc};
+        cudaKernelNodeParams kp{};
+        kp.func = const_cast<void *>(hf::trace_batched_fn(shadows, stats));
+        kp.gridDim = dim3((unsigned)(c->sm_count * c->occ[shadows][stats]));
+        kp.blockDim = dim3(hf::kThreads);
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = args;
+        if (cudaGraphAddKernelNode(&kern, graph, &copy, 1, &kp) != cudaSuccess ||
+            cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+            (void)cudaGetLastError();
+            cudaGraphDestroy(graph);
+            return HF_E_CUDA;
+        }
+        cudaGraphDestroy(graph);
+        if ((int)s.graphs.size() >= kMaxGraphsPerSlot) {
+            cudaGraphExecDestroy(s.graphs.front().second);
+            s.graphs.erase(s.graphs.begin());
+        }
+        s.graphs.push_back({key, exec});
+    }
+    CK(cudaGraphLaunch(exec, stream));
+    return HF_OK;
+}
+
+int hf_render(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_outputs *outs,
+              const hf_render_opts *opts) {
+    if (!c) return HF_E_INVALID_ARG;
+    if (n == 0) return HF_OK;
+    if (!cams || !outs || n > HF_MAX_CAMERAS) return HF_E_INVALID_ARG;
+    hf_render_opts o{};
+    if (opts) o = *opts;
+    else o.mip_start = HF_MIP_AUTO;
+    const uint32_t tw = o.tile_w ? o.tile_w : 8, th = o.tile_h ? o.tile_h : 4;
+    const int twl = ilog2_exact(tw), thl = ilog2_exact(th);
+    if (twl < 0 || thl < 0 || tw * th < 32 || tw * th > 256 || tw > 256 || th > 256)
+        return HF_E_INVALID_ARG;
+    int32_t sun[3] = {o.sun[0], o.sun[1], o.sun[2]};
+    if (sun[0] == 0 && sun[1] == 0 && sun[2] == 0)
+        for (int i = 0; i < 3; ++i) sun[i] = kDefaultSun[i];
+    for (int i = 0; i < 3; ++i)
+        if (iabs64(sun[i]) >= kLimit21) return HF_E_INVALID_ARG;
+    uint64_t total_tiles = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        if (hf_validate_camera(c->W, c->H, &cams[i]) != HF_OK) return HF_E_INVALID_ARG;
+        const uint64_t tx = (cams[i].w + tw - 1) / tw, ty = (cams[i].h + th - 1) / th;
+        total_tiles += tx * ty;
+    }
+    if (total_tiles >= 0xFFFFFFFFull) return HF_E_INVALID_ARG;
+    const bool shadows = (o.flags & HF_SHADOWS) != 0;
+    const bool stats = (o.flags & HF_STATS) != 0;
+    const uint32_t mip = o.mip_start == HF_MIP_AUTO ? kDefaultMip : o.mip_start;
+    const uint32_t mip_c = mip > c->L ? c->L : mip;
+    const uint64_t guard = 4ull * (c->W + c->H) + 64;
+    const uint32_t steps = o.max_steps ? o.max_steps : (uint32_t)(guard > 0x7FFFFFFF ? 0x7FFFFFFF : guard);
+    if (steps > 0x7FFFFFFFu) return HF_E_INVALID_ARG;
+
+    CK(cudaSetDevice(c->device));
+    cudaStream_t stream = o.cuda_stream ? (cudaStream_t)o.cuda_stream : c->stream;
+    int si = 0;
+    int rc = acquire_slot(c, (o.flags & HF_NOWAIT) != 0, &si);
+    if (rc != HF_OK) return rc;
+    Slot &s = c->slots[si];
+    const size_t bytes = sizeof(hf::BatchHeader) + (size_t)n * sizeof(hf::CamDev);
+    const size_t bucket = (bytes + kScratchAlign - 1) & ~(kScratchAlign - 1);
+    rc = ensure_slot_cap(s, bucket);
+    if (rc != HF_OK) return rc;
+
+    auto *hdr = (hf::BatchHeader *)s.h_staging;
+    std::memset(hdr, 0, sizeof(*hdr));
+    hdr->n_cams = n;
+    hdr->total_tiles = (uint32_t)total_tiles;
+    auto *cd = (hf::CamDev *)((char *)s.h_staging + sizeof(hf::BatchHeader));
+    std::vector<uint32_t> tiles(n);
+    uint32_t base = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        const hf_camera &k = cams[i];
+        hf::CamDev &v = cd[i];
+        for (int a = 0; a < 3; ++a) {
+            v.o[a] = (int32_t)k.origin[a];
+            v.F[a] = k.fwd[a];
+            v.R[a] = k.right[a];
+            v.U[a] = k.up[a];
+        }
+        v.w = k.w;
+        v.h = k.h;
+        v.tiles_x = (k.w + tw - 1) / tw;
+        tiles[i] = v.tiles_x * ((k.h + th - 1) / th);
+        v.tile_base = base;
+        base += tiles[i];
+        v.hit_cell = outs[i].hit_cell;
+        v.layer = outs[i].layer;
+        v.face = outs[i].face;
+        v.depth = outs[i].depth;
+        v.rgba = outs[i].rgba;
+        v.shadow = outs[i].shadow;
+    }
+
+    hf::RenderParams p{};
+    p.world = c->wd;
+    p.hdr = (hf::BatchHeader *)s.d_scratch;
+    p.cams = (const hf::CamDev *)((char *)s.d_scratch + sizeof(hf::BatchHeader));
+    p.status = c->d_status;
+    p.stats = c->d_stats;
+    p.tile_w_log2 = twl;
+    p.tile_h_log2 = thl;
+    p.mip_start = (int32_t)mip_c;
+    p.max_steps = (int32_t)steps;
+    const double sn = std::sqrt((double)sun[0] * sun[0] + (double)sun[1] * sun[1] +
+                                (double)sun[2] * sun[2]);
+    for (int i = 0; i < 3; ++i) {
+        p.sun[i] = sun[i];
+        p.sun_n[i] = (float)(sun[i] / sn);
+    }
+
+    if (stream != c->stream) CK(cudaStreamWaitEvent(stream, c->edit_done, 0));
+    if (o.flags & HF_PLAIN) {
+        CK(cudaMemcpyAsync(s.d_scratch, s.h_staging, bytes, cudaMemcpyHostToDevice, stream));
+        for (uint32_t i = 0; i < n; ++i)
+            if (hf::launch_trace_plain(p, shadows, stats, i, tiles[i], stream)) return HF_E_CUDA;
+    } else if (o.flags & HF_NOGRAPH) {
+        CK(cudaMemcpyAsync(s.d_scratch, s.h_staging, bytes, cudaMemcpyHostToDevice, stream));
+        if (hf::launch_trace_batched(p, shadows, stats, c->sm_count * c->occ[shadows][stats],
+                                     stream))
+            return HF_E_CUDA;
+    } else {
+        GraphKey key{};
+        key.bytes = (uint32_t)bucket;
+        key.shadows = shadows;
+        key.stats = stats;
+        key.twl = (uint32_t)twl;
+        key.thl = (uint32_t)thl;
+        key.mip = mip_c;
+        key.steps = steps;
+        for (int i = 0; i < 3; ++i) key.sun[i] = sun[i];
+        rc = launch_graph(c, s, key, p, shadows, stats, stream);
+        if (rc != HF_OK) return rc;
+    }
+    CK(cudaEventRecord(s.done, stream));
+    s.pending = true;
+    if (o.flags & HF_SYNC) {
+        CK(cudaEventSynchronize(s.done));
+        s.pending = false;
+        return read_status(c);
+    }
+    return HF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,77 @@
+// hf_internal.h -- device-side structures shared by the kernels and the C ABI.
+//
+// Memory layout in HBM (one allocation per context, 256-byte aligned levels):
+//   level 0   : the cells, W x H uint32 words, row-major y*W + x
+//   level k>=1: ceil(W/2^k) x ceil(H/2^k) node words, row-major,
+//               byte0 max h0, byte1 min (slab ? h1 : 255), byte2 max (slab ? h2 : h0)
+// Per-render scratch (one block per render slot):
+//   BatchHeader (tile counter, camera count, tile count), then CamDev[n].
+#pragma once
+
+#include <cstdint>
+
+namespace hf {
+
+constexpr int kMaxLevels = 14;  // 2^14 = 16384 = largest grid side
+constexpr int kShift = 16;      // 2^16 fixed-point units per world unit
+constexpr int kThreads = 128;   // threads per trace block (4 warps)
+constexpr uint32_t kMaxCams = 4096;
+
+constexpr uint8_t kFaceNX = 0, kFacePX = 1, kFaceNY = 2, kFacePY = 3, kFaceNZ = 4, kFacePZ = 5,
+                  kFaceInside = 6, kFaceError = 254, kFaceMiss = 255;
+
+struct WorldDev {
+    const uint32_t *base;               // level 0 at base, level k at base + off[k]
+    uint32_t off[kMaxLevels + 1];       // word offset of each level
+    uint32_t stride[kMaxLevels + 1];    // words per row of each level
+    int32_t W, H, L;                    // grid size, top level
+};
+
+struct CamDev {
+    int32_t o[3];
+    int32_t F[3], R[3], U[3];
+    uint32_t w, h;
+    uint32_t tiles_x, tile_base;  // tiles per image row, first global tile of this camera
+    uint32_t *hit_cell;
+    uint8_t *layer;
+    uint8_t *face;
+    float *depth;
+    uint32_t *rgba;
+    uint8_t *shadow;
+};
+
+struct BatchHeader {
+    uint32_t counter;      // next global tile (atomic, zero at launch)
+    uint32_t n_cams;
+    uint32_t total_tiles;
+    uint32_t pad[29];      // CamDev array starts 128 bytes in
+};
+static_assert(sizeof(BatchHeader) == 128, "header size");
+
+struct RenderParams {
+    WorldDev world;
+    BatchHeader *hdr;              // per-slot scratch header (batched kernel)
+    const CamDev *cams;            // per-slot camera table
+    uint32_t *status;              // bit 0: a ray hit its step guard
+    unsigned long long *stats;     // 5 counters (HF_STATS)
+    int32_t tile_w_log2, tile_h_log2;
+    int32_t mip_start;
+    int32_t max_steps;
+    int32_t sun[3];
+    float sun_n[3];                // sun / |sun|
+};
+
+// Launch wrappers (hf_trace.cu)
+int launch_trace_batched(const RenderParams &p, bool shadows, bool stats, int blocks,
+                         void *stream);
+int launch_trace_plain(const RenderParams &p, bool shadows, bool stats, uint32_t cam_index,
+                       uint32_t n_tiles, void *stream);
+const void *trace_batched_fn(bool shadows, bool stats);
+int trace_batched_occupancy(bool shadows, bool stats, int *blocks_per_sm);
+
+// Pyramid (hf_pyramid.cu): repair the nodes covering cell rectangle
+// [x0, x1) x [y0, y1) at every level 1..L, in order.
+int pyramid_repair(uint32_t *world, const WorldDev &w, int32_t x0, int32_t y0, int32_t x1,
+                   int32_t y1, void *stream);
+
+}  // namespace hf

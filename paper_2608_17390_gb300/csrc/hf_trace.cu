@@ -1,0 +1,498 @@
+// hf_trace.cu -- per-pixel exact ray casting through a two-interval height field.
+//
+// One warp owns one tile of tile_w x tile_h pixels; each lane traces the
+// tile's pixels lane, lane+32, ...  Every branch of the traversal is decided
+// with exact integer arithmetic on 32-bit operands and 64-bit products, so hit
+// cell, layer and face equal the definition bit for bit:
+//
+//   * ray generation: d = F + (2px+1-w) R + (h-1-2py) U (int32, bounded < 2^21);
+//   * times are rationals num/den with 0 <= num <= 2^30 and 0 < den < 2^21;
+//   * "z(t) vs h S" is the sign of (oz - hS) den + num dz (|.| < 2^52);
+//   * hierarchical DDA over the min/max pyramid: a node whose ray segment lies
+//     above its highest top, or above every floor and below every slab
+//     underside, is skipped to its exit (the hierarchy may only skip
+//     known-empty space, Section 3.2 of the paper); otherwise the traversal
+//     descends; at level 0 the cell's two solid intervals are tested (the
+//     SOLID predicate of Section 3.1, closed ends, floor unbounded below);
+//   * after a node skip the coordinate along the other axis is an exact floor
+//     division with a float estimate and one integer correction.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "hf_internal.h"
+
+namespace hf {
+namespace {
+
+__constant__ float c_albedo[8][3] = {
+    {0.55f, 0.50f, 0.40f}, {0.35f, 0.55f, 0.25f}, {0.60f, 0.60f, 0.62f}, {0.80f, 0.72f, 0.50f},
+    {0.30f, 0.30f, 0.32f}, {0.70f, 0.35f, 0.20f}, {0.90f, 0.90f, 0.95f}, {0.25f, 0.40f, 0.60f},
+};
+constexpr float kKa = 0.3f, kKd = 0.7f;
+constexpr uint32_t kSky = 0xFFEBB487u;  // r 135, g 180, b 235, a 255
+
+struct Ray {
+    int32_t ox, oy, oz, dx, dy, dz;
+};
+
+struct Hit {
+    int32_t cx, cy;
+    int32_t tnum, tden;  // hit time tnum / tden
+    uint32_t word;       // hit cell word
+    uint8_t layer, face;
+};
+
+struct Counters {
+    uint32_t nodes, cells;
+};
+
+// sign carrier of z(t) - h S for t = num / den (den > 0):  (oz - hS) den + num dz
+__device__ __forceinline__ int64_t zd(int32_t oz_minus_hs, int32_t dz, int32_t num, int32_t den) {
+    return (int64_t)oz_minus_hs * den + (int64_t)num * dz;
+}
+
+// floor(Q / a) for 0 <= Q < 2^36, 1 <= a < 2^21, quotient < 2^15; r = remainder.
+__device__ __forceinline__ int32_t floor_quot(int64_t Q, int32_t a, float rcp_a, int64_t &r) {
+    int32_t q = (int32_t)((float)Q * rcp_a);
+    r = Q - (int64_t)q * a;
+    if (r < 0) {
+        q -= 1;
+        r += a;
+    } else if (r >= a) {
+        q += 1;
+        r -= a;
+    }
+    return q;
+}
+
+__device__ __forceinline__ int64_t floor_div64(int64_t a, int32_t b) {  // b > 0
+    int64_t q = a / b;
+    if ((a % b) != 0 && a < 0) q -= 1;
+    return q;
+}
+
+__device__ __forceinline__ uint32_t load_word(const WorldDev &w, int level, int32_t x, int32_t y) {
+    return __ldg(w.base + w.off[level] + (uint32_t)y * w.stride[level] + (uint32_t)x);
+}
+
+// The two-interval test of one cell over [tin, tout] (tout finite).
+// Returns true and fills h on a hit.
+__device__ __forceinline__ bool leaf_test(const Ray &r, uint32_t word, int32_t tin_num,
+                                          int32_t tin_den, int32_t tout_num, int32_t tout_den,
+                                          uint8_t entry_face, Hit &h) {
+    const int32_t h0 = word & 0xFF, h1 = (word >> 8) & 0xFF, h2 = (word >> 16) & 0xFF;
+    const bool slab = h1 > h0;
+    const int32_t a0 = r.oz - (h0 << kShift);
+    const int64_t zin0 = zd(a0, r.dz, tin_num, tin_den);
+    if (zin0 <= 0) {
+        h.layer = 0;
+        h.face = entry_face;
+        h.tnum = tin_num;
+        h.tden = tin_den;
+        return true;
+    }
+    const int32_t a1 = r.oz - (h1 << kShift), a2 = r.oz - (h2 << kShift);
+    int64_t zin1 = 0, zin2 = 0;
+    if (slab) {
+        zin1 = zd(a1, r.dz, tin_num, tin_den);
+        zin2 = zd(a2, r.dz, tin_num, tin_den);
+        if (zin1 >= 0 && zin2 <= 0) {
+            h.layer = 1;
+            h.face = entry_face;
+            h.tnum = tin_num;
+            h.tden = tin_den;
+            return true;
+        }
+    }
+    if (r.dz < 0) {
+        if (slab && zin2 > 0 && zd(a2, r.dz, tout_num, tout_den) <= 0) {
+            h.layer = 1;
+            h.face = kFacePZ;
+            h.tnum = a2;
+            h.tden = -r.dz;
+            return true;
+        }
+        if (zd(a0, r.dz, tout_num, tout_den) <= 0) {
+            h.layer = 0;
+            h.face = kFacePZ;
+            h.tnum = a0;
+            h.tden = -r.dz;
+            return true;
+        }
+    } else if (r.dz > 0) {
+        if (slab && zin1 < 0 && zd(a1, r.dz, tout_num, tout_den) >= 0) {
+            h.layer = 1;
+            h.face = kFaceNZ;
+            h.tnum = -a1;
+            h.tden = r.dz;
+            return true;
+        }
+    }
+    return false;
+}
+
+// A vertical ray (dx = dy = 0) stays in its start column for all t >= 0.
+__device__ __forceinline__ bool vertical_test(const Ray &r, uint32_t word, Hit &h) {
+    const int32_t h0 = word & 0xFF, h1 = (word >> 8) & 0xFF, h2 = (word >> 16) & 0xFF;
+    const bool slab = h1 > h0;
+    const int32_t a0 = r.oz - (h0 << kShift), a1 = r.oz - (h1 << kShift),
+                  a2 = r.oz - (h2 << kShift);
+    h.face = kFaceInside;
+    h.tnum = 0;
+    h.tden = 1;
+    if (a0 <= 0) {
+        h.layer = 0;
+        return true;
+    }
+    if (slab && a1 >= 0 && a2 <= 0) {
+        h.layer = 1;
+        return true;
+    }
+    if (r.dz < 0) {
+        h.face = kFacePZ;
+        h.tden = -r.dz;
+        if (slab && a2 > 0) {
+            h.layer = 1;
+            h.tnum = a2;
+        } else {
+            h.layer = 0;
+            h.tnum = a0;
+        }
+        return true;
+    }
+    if (r.dz > 0 && slab && a1 < 0) {
+        h.layer = 1;
+        h.face = kFaceNZ;
+        h.tnum = -a1;
+        h.tden = r.dz;
+        return true;
+    }
+    return false;
+}
+
+// Exact first hit of one ray.  h.face = kFaceMiss on a miss, kFaceError when
+// max_steps iterations did not finish the ray.
+template <bool STATS>
+__device__ __forceinline__ void trace_ray(const WorldDev &w, const Ray &r, int mip_start,
+                                          int max_steps, Hit &h, Counters &cnt) {
+    h.face = kFaceMiss;
+    h.layer = 255;
+    const int sx = (r.dx > 0) - (r.dx < 0), sy = (r.dy > 0) - (r.dy < 0);
+    const int32_t adx = abs(r.dx), ady = abs(r.dy);
+    int32_t cx = r.ox >> kShift, cy = r.oy >> kShift;
+    if (r.dx < 0 && (r.ox & 0xFFFF) == 0) cx -= 1;
+    if (r.dy < 0 && (r.oy & 0xFFFF) == 0) cy -= 1;
+    if ((uint32_t)cx >= (uint32_t)w.W || (uint32_t)cy >= (uint32_t)w.H) return;
+
+    if (adx == 0 && ady == 0) {
+        const uint32_t word = load_word(w, 0, cx, cy);
+        if (STATS) cnt.cells++;
+        if (vertical_test(r, word, h)) {
+            h.cx = cx;
+            h.cy = cy;
+            h.word = word;
+        }
+        return;
+    }
+
+    const float rcpx = adx ? 1.0f / (float)adx : 0.0f;
+    const float rcpy = ady ? 1.0f / (float)ady : 0.0f;
+    int32_t tin_num = 0, tin_den = 1;
+    uint8_t entry = kFaceInside;
+    int level = mip_start;
+
+    for (int it = 0; it < max_steps; ++it) {
+        const int32_t nx = cx >> level, ny = cy >> level;
+        const int32_t bx = (sx > 0 ? nx + 1 : nx) << level;  // exit boundary (cells)
+        const int32_t by = (sy > 0 ? ny + 1 : ny) << level;
+        const int32_t numx = sx > 0 ? (bx << kShift) - r.ox : (sx < 0 ? r.ox - (bx << kShift) : 1);
+        const int32_t numy = sy > 0 ? (by << kShift) - r.oy : (sy < 0 ? r.oy - (by << kShift) : 1);
+        const int64_t cmp = (int64_t)numx * ady - (int64_t)numy * adx;  // < 0: x exits first
+        const bool xfirst = cmp <= 0;
+        const int32_t tout_num = xfirst ? numx : numy;
+        const int32_t tout_den = xfirst ? adx : ady;
+        const uint32_t word = load_word(w, level, nx, ny);
+
+        if (level > 0) {
+            if (STATS) cnt.nodes++;
+            const int32_t maxh0 = word & 0xFF, minh1 = (word >> 8) & 0xFF,
+                          maxtop = (word >> 16) & 0xFF;
+            const bool down = r.dz < 0;
+            const int32_t lo_num = down ? tout_num : tin_num, lo_den = down ? tout_den : tin_den;
+            const int32_t hi_num = down ? tin_num : tout_num, hi_den = down ? tin_den : tout_den;
+            const bool empty =
+                zd(r.oz - (maxtop << kShift), r.dz, lo_num, lo_den) > 0 ||
+                (zd(r.oz - (maxh0 << kShift), r.dz, lo_num, lo_den) > 0 &&
+                 zd(r.oz - (minh1 << kShift), r.dz, hi_num, hi_den) < 0);
+            if (!empty) {
+                --level;
+                continue;
+            }
+        } else {
+            if (STATS) cnt.cells++;
+            if (leaf_test(r, word, tin_num, tin_den, tout_num, tout_den, entry, h)) {
+                h.cx = cx;
+                h.cy = cy;
+                h.word = word;
+                return;
+            }
+        }
+
+        // advance past the node (or cell) through its exit side
+        int32_t ncx = cx, ncy = cy;
+        bool corner = false;
+        if (cmp < 0) {
+            ncx = sx > 0 ? bx : bx - 1;
+            if (level > 0) {
+                const int32_t y0 = ny << level;
+                const int64_t E = (int64_t)(r.oy - (y0 << kShift)) * adx + (int64_t)numx * r.dy;
+                int64_t rem;
+                const int32_t q = floor_quot(E >> kShift, adx, rcpx, rem);
+                const bool exact = ((E & 0xFFFF) == 0) && rem == 0;
+                ncy = y0 + q - ((sy < 0 && exact) ? 1 : 0);
+            }
+            entry = sx > 0 ? kFaceNX : kFacePX;
+        } else if (cmp > 0) {
+            ncy = sy > 0 ? by : by - 1;
+            if (level > 0) {
+                const int32_t x0 = nx << level;
+                const int64_t E = (int64_t)(r.ox - (x0 << kShift)) * ady + (int64_t)numy * r.dx;
+                int64_t rem;
+                const int32_t q = floor_quot(E >> kShift, ady, rcpy, rem);
+                const bool exact = ((E & 0xFFFF) == 0) && rem == 0;
+                ncx = x0 + q - ((sx < 0 && exact) ? 1 : 0);
+                // x lands exactly on a cell boundary while moving in x: the
+                // cell-level walk crosses a corner here, whose entry face is X
+                corner = exact && sx != 0;
+            }
+            entry = corner ? (sx > 0 ? kFaceNX : kFacePX) : (sy > 0 ? kFaceNY : kFacePY);
+        } else {  // exact corner: both axes change
+            ncx = sx > 0 ? bx : bx - 1;
+            ncy = sy > 0 ? by : by - 1;
+            entry = sx > 0 ? kFaceNX : kFacePX;
+        }
+        cx = ncx;
+        cy = ncy;
+        tin_num = tout_num;
+        tin_den = tout_den;
+        if ((uint32_t)cx >= (uint32_t)w.W || (uint32_t)cy >= (uint32_t)w.H) return;
+        if (level < mip_start) {  // ascend when the crossed boundary is a parent boundary
+            const int32_t bnd = cmp <= 0 ? bx : by;
+            if ((bnd & ((2 << level) - 1)) == 0) ++level;
+        }
+    }
+    h.face = kFaceError;
+    h.layer = 255;
+}
+
+__device__ __forceinline__ uint32_t shade(uint32_t word, uint8_t face, bool visible,
+                                          const float *ln) {
+    float ndl;
+    switch (face) {
+        case kFaceNX: ndl = -ln[0]; break;
+        case kFacePX: ndl = ln[0]; break;
+        case kFaceNY: ndl = -ln[1]; break;
+        case kFacePY: ndl = ln[1]; break;
+        case kFaceNZ: ndl = -ln[2]; break;
+        case kFacePZ: ndl = ln[2]; break;
+        default: ndl = 0.0f;
+    }
+    const float k = kKa + kKd * fmaxf(ndl, 0.0f) * (visible ? 1.0f : 0.0f);
+    const uint32_t m = (word >> 24) & 7;
+    uint32_t out = 0xFF000000u;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        const float v = fminf(fmaxf(c_albedo[m][ch] * k, 0.0f), 1.0f);
+        out |= ((uint32_t)(255.0f * v + 0.5f)) << (8 * ch);
+    }
+    return out;
+}
+
+template <bool SHADOWS, bool STATS>
+__device__ __forceinline__ void trace_pixel(const RenderParams &p, const CamDev &c, int32_t px,
+                                            int32_t py, Counters &cnt, Counters &scnt,
+                                            uint32_t &nshadow, bool &err) {
+    const int32_t a = 2 * px + 1 - (int32_t)c.w;
+    const int32_t b = (int32_t)c.h - 1 - 2 * py;
+    Ray r;
+    r.ox = c.o[0];
+    r.oy = c.o[1];
+    r.oz = c.o[2];
+    r.dx = c.F[0] + a * c.R[0] + b * c.U[0];
+    r.dy = c.F[1] + a * c.R[1] + b * c.U[1];
+    r.dz = c.F[2] + a * c.R[2] + b * c.U[2];
+    Hit h;
+    trace_ray<STATS>(p.world, r, p.mip_start, p.max_steps, h, cnt);
+    const uint32_t pix = (uint32_t)py * c.w + (uint32_t)px;
+    const bool hit = h.face < kFaceError;
+    if (h.face == kFaceError) err = true;
+    bool visible = true;
+    if (SHADOWS && hit) {
+        if (h.face == kFaceInside) {
+            visible = false;
+        } else {
+            Ray s;
+            int64_t px64 = (int64_t)r.ox + floor_div64((int64_t)h.tnum * r.dx, h.tden);
+            int64_t py64 = (int64_t)r.oy + floor_div64((int64_t)h.tnum * r.dy, h.tden);
+            int64_t pz64 = (int64_t)r.oz + floor_div64((int64_t)h.tnum * r.dz, h.tden);
+            switch (h.face) {
+                case kFaceNX: px64 -= 1; break;
+                case kFacePX: px64 += 1; break;
+                case kFaceNY: py64 -= 1; break;
+                case kFacePY: py64 += 1; break;
+                case kFaceNZ: pz64 -= 1; break;
+                default: pz64 += 1; break;
+            }
+            s.ox = (int32_t)px64;
+            s.oy = (int32_t)py64;
+            s.oz = (int32_t)pz64;
+            s.dx = p.sun[0];
+            s.dy = p.sun[1];
+            s.dz = p.sun[2];
+            Hit sh;
+            if (STATS) nshadow++;
+            if (px64 >= 0 && py64 >= 0) {
+                trace_ray<STATS>(p.world, s, p.mip_start, p.max_steps, sh, scnt);
+                if (sh.face == kFaceError) err = true;
+                visible = sh.face == kFaceMiss;
+            }
+        }
+        if (c.shadow) __stcs(c.shadow + pix, (uint8_t)(visible ? 0 : 1));
+    }
+    if (c.hit_cell) __stcs(c.hit_cell + pix, hit ? (uint32_t)h.cy * (uint32_t)p.world.W + (uint32_t)h.cx : 0xFFFFFFFFu);
+    if (c.layer) __stcs(c.layer + pix, hit ? h.layer : (uint8_t)255);
+    if (c.face) __stcs(c.face + pix, h.face);
+    if (c.depth) {
+        float dep = __int_as_float(0x7f800000);
+        if (hit) {
+            const float fx = (float)r.dx, fy = (float)r.dy, fz = (float)r.dz;
+            const float n = sqrtf(fx * fx + fy * fy + fz * fz);
+            dep = ((float)h.tnum / (float)h.tden) * n * (1.0f / 65536.0f);
+        }
+        __stcs(c.depth + pix, dep);
+    }
+    if (c.rgba) __stcs(c.rgba + pix, hit ? shade(h.word, h.face, visible, p.sun_n) : kSky);
+}
+
+template <bool SHADOWS, bool STATS>
+__device__ __forceinline__ void trace_tile(const RenderParams &p, const CamDev &c,
+                                           uint32_t local_tile, int lane) {
+    const uint32_t tx = local_tile % c.tiles_x, ty = local_tile / c.tiles_x;
+    const int32_t tw_log2 = p.tile_w_log2;
+    const int32_t x0 = (int32_t)tx << tw_log2, y0 = (int32_t)ty << p.tile_h_log2;
+    const int32_t npix = 1 << (tw_log2 + p.tile_h_log2);
+    Counters cnt{0, 0}, scnt{0, 0};
+    uint32_t nshadow = 0, nrays = 0;
+    bool err = false;
+    for (int i = lane; i < npix; i += 32) {
+        const int32_t px = x0 + (i & ((1 << tw_log2) - 1));
+        const int32_t py = y0 + (i >> tw_log2);
+        if (px < (int32_t)c.w && py < (int32_t)c.h) {
+            trace_pixel<SHADOWS, STATS>(p, c, px, py, cnt, scnt, nshadow, err);
+            if (STATS) nrays++;
+        }
+    }
+    if (__any_sync(0xFFFFFFFFu, err) && lane == 0) atomicOr(p.status, 1u);
+    if (STATS) {
+        const uint32_t vn = __reduce_add_sync(0xFFFFFFFFu, cnt.nodes);
+        const uint32_t vc = __reduce_add_sync(0xFFFFFFFFu, cnt.cells);
+        const uint32_t vr = __reduce_add_sync(0xFFFFFFFFu, nrays);
+        const uint32_t vs = __reduce_add_sync(0xFFFFFFFFu, nshadow);
+        const uint32_t vf = __reduce_add_sync(0xFFFFFFFFu, scnt.nodes + scnt.cells);
+        if (lane == 0) {
+            atomicAdd(p.stats + 0, (unsigned long long)vn);
+            atomicAdd(p.stats + 1, (unsigned long long)vc);
+            atomicAdd(p.stats + 2, (unsigned long long)vr);
+            atomicAdd(p.stats + 3, (unsigned long long)vs);
+            atomicAdd(p.stats + 4, (unsigned long long)vf);
+        }
+    }
+}
+
+__device__ __forceinline__ CamDev load_cam(const CamDev *cams, uint32_t i) { return cams[i]; }
+
+// Persistent batched kernel: warps pop (camera, tile) items from one atomic
+// counter until the batch is drained.  One launch renders every camera.
+template <bool SHADOWS, bool STATS>
+__global__ void __launch_bounds__(kThreads) k_trace_batched(const RenderParams p) {
+    __shared__ uint32_t s_base[kMaxCams + 1];
+    const uint32_t n = p.hdr->n_cams;
+    const uint32_t total = p.hdr->total_tiles;
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) s_base[i] = p.cams[i].tile_base;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(&p.hdr->counter, 1u);
+        t = __shfl_sync(0xFFFFFFFFu, t, 0);
+        if (t >= total) break;
+        // last camera whose first tile is <= t
+        uint32_t lo = 0, hi = n;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (s_base[mid] <= t) lo = mid;
+            else hi = mid;
+        }
+        const CamDev c = load_cam(p.cams, lo);
+        trace_tile<SHADOWS, STATS>(p, c, t - s_base[lo], lane);
+    }
+}
+
+// Plain kernel: one camera, one warp per tile, grid covers the image once.
+template <bool SHADOWS, bool STATS>
+__global__ void __launch_bounds__(kThreads) k_trace_plain(const RenderParams p, uint32_t cam,
+                                                          uint32_t n_tiles) {
+    const uint32_t t = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    if (t >= n_tiles) return;
+    const CamDev c = load_cam(p.cams, cam);
+    trace_tile<SHADOWS, STATS>(p, c, t, threadIdx.x & 31);
+}
+
+template <bool SH, bool ST>
+const void *batched_ptr() {
+    return reinterpret_cast<const void *>(&k_trace_batched<SH, ST>);
+}
+
+}  // namespace
+
+const void *trace_batched_fn(bool shadows, bool stats) {
+    if (shadows) return stats ? batched_ptr<true, true>() : batched_ptr<true, false>();
+    return stats ? batched_ptr<false, true>() : batched_ptr<false, false>();
+}
+
+int trace_batched_occupancy(bool shadows, bool stats, int *blocks_per_sm) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        blocks_per_sm, trace_batched_fn(shadows, stats), kThreads, 0);
+    return e == cudaSuccess ? 0 : -1;
+}
+
+int launch_trace_batched(const RenderParams &p, bool shadows, bool stats, int blocks,
+                         void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (shadows) {
+        if (stats) k_trace_batched<true, true><<<blocks, kThreads, 0, s>>>(p);
+        else k_trace_batched<true, false><<<blocks, kThreads, 0, s>>>(p);
+    } else {
+        if (stats) k_trace_batched<false, true><<<blocks, kThreads, 0, s>>>(p);
+        else k_trace_batched<false, false><<<blocks, kThreads, 0, s>>>(p);
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_trace_plain(const RenderParams &p, bool shadows, bool stats, uint32_t cam,
+                       uint32_t n_tiles, void *stream) {
+    if (n_tiles == 0) return 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint32_t warps = kThreads / 32;
+    const uint32_t blocks = (n_tiles + warps - 1) / warps;
+    if (shadows) {
+        if (stats) k_trace_plain<true, true><<<blocks, kThreads, 0, s>>>(p, cam, n_tiles);
+        else k_trace_plain<true, false><<<blocks, kThreads, 0, s>>>(p, cam, n_tiles);
+    } else {
+        if (stats) k_trace_plain<false, true><<<blocks, kThreads, 0, s>>>(p, cam, n_tiles);
+        else k_trace_plain<false, false><<<blocks, kThreads, 0, s>>>(p, cam, n_tiles);
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace hf
