@@ -48,11 +48,11 @@ def _dist():
 
 # ------------------------------------------------------------------ workloads
 
-def workload(name, rank=0):
+def workload(name, rank=0, scale=1):
     import synth
 
     if name == "c3":
-        cfg = synth.config_c3()
+        cfg = synth.config_c3(scale=scale)
         return dict(name="C3 batched cameras: 2048x2048 walls+caves grid (seed 2), 64 cameras "
                          "(16x3840x2160, 24x1920x1080, 24x640x360), shadow rays on, one 64x64 "
                          "crater edit + incremental pyramid repair per step",
@@ -174,7 +174,9 @@ def run_hf(args):
     import paper_2608_17390_gb300 as hf
     import synth
 
-    wl = workload(args.workload, rank)
+    wl = workload(args.workload, rank, args.scale)
+    if args.scale != 1:
+        wl["name"] += " (resolutions divided by %d)" % args.scale
     cells = wl["cells"].copy()
     cams_all = wl["cams"]
     fps = wl.get("frames_per_step")
@@ -388,6 +390,8 @@ def main():
     ap.add_argument("--tile-w", type=int, default=0)
     ap.add_argument("--tile-h", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--scale", type=int, default=1,
+                    help="divide the batched workload's resolutions (small profiling cases)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -132,42 +132,38 @@ __device__ __forceinline__ bool leaf_test(const Ray &r, uint32_t word, int32_t t
 }
 
 // A vertical ray (dx = dy = 0) stays in its start column for all t >= 0.
+// Writes h only when the ray hits.
 __device__ __forceinline__ bool vertical_test(const Ray &r, uint32_t word, Hit &h) {
     const int32_t h0 = word & 0xFF, h1 = (word >> 8) & 0xFF, h2 = (word >> 16) & 0xFF;
     const bool slab = h1 > h0;
     const int32_t a0 = r.oz - (h0 << kShift), a1 = r.oz - (h1 << kShift),
                   a2 = r.oz - (h2 << kShift);
-    h.face = kFaceInside;
-    h.tnum = 0;
-    h.tden = 1;
+    uint8_t layer, face;
+    int32_t tnum = 0, tden = 1;
     if (a0 <= 0) {
-        h.layer = 0;
-        return true;
+        layer = 0;
+        face = kFaceInside;
+    } else if (slab && a1 >= 0 && a2 <= 0) {
+        layer = 1;
+        face = kFaceInside;
+    } else if (r.dz < 0) {
+        face = kFacePZ;
+        tden = -r.dz;
+        layer = (slab && a2 > 0) ? 1 : 0;
+        tnum = layer ? a2 : a0;
+    } else if (r.dz > 0 && slab && a1 < 0) {
+        layer = 1;
+        face = kFaceNZ;
+        tnum = -a1;
+        tden = r.dz;
+    } else {
+        return false;
     }
-    if (slab && a1 >= 0 && a2 <= 0) {
-        h.layer = 1;
-        return true;
-    }
-    if (r.dz < 0) {
-        h.face = kFacePZ;
-        h.tden = -r.dz;
-        if (slab && a2 > 0) {
-            h.layer = 1;
-            h.tnum = a2;
-        } else {
-            h.layer = 0;
-            h.tnum = a0;
-        }
-        return true;
-    }
-    if (r.dz > 0 && slab && a1 < 0) {
-        h.layer = 1;
-        h.face = kFaceNZ;
-        h.tnum = -a1;
-        h.tden = r.dz;
-        return true;
-    }
-    return false;
+    h.layer = layer;
+    h.face = face;
+    h.tnum = tnum;
+    h.tden = tden;
+    return true;
 }
 
 // Exact first hit of one ray.  h.face = kFaceMiss on a miss, kFaceError when
@@ -357,8 +353,8 @@ __device__ __forceinline__ void trace_pixel(const RenderParams &p, const CamDev 
                 visible = sh.face == kFaceMiss;
             }
         }
-        if (c.shadow) __stcs(c.shadow + pix, (uint8_t)(visible ? 0 : 1));
     }
+    if (SHADOWS && c.shadow) __stcs(c.shadow + pix, (uint8_t)(visible ? 0 : 1));
     if (c.hit_cell) __stcs(c.hit_cell + pix, hit ? (uint32_t)h.cy * (uint32_t)p.world.W + (uint32_t)h.cx : 0xFFFFFFFFu);
     if (c.layer) __stcs(c.layer + pix, hit ? h.layer : (uint8_t)255);
     if (c.face) __stcs(c.face + pix, h.face);

@@ -292,7 +292,7 @@ def test_pyramid_build_and_repair_equal_rebuild(hf):
                     w, h = W, H
                 x0 = int(rng.integers(0, W - w + 1))
                 y0 = int(rng.integers(0, H - h + 1))
-                blk = _rand_grid(rng, w, h, 250)
+                blk = _rand_grid(rng, w, h, 240)
                 hf.hf_edit(ctx, x0, y0, blk)
                 cells[y0:y0 + h, x0:x0 + w] = blk
             hf.hf_sync(ctx)
