@@ -162,6 +162,37 @@ int hf_edit(hf_ctx *ctx, uint32_t x0, uint32_t y0, uint32_t w, uint32_t h,
 int hf_render(hf_ctx *ctx, const hf_camera *cams, uint32_t n, const hf_outputs *outs,
               const hf_render_opts *opts);
 
+/* Allocation-free variant of hf_render.  The paper has no counterpart; it is
+ * here for callers that must not allocate device memory while they run: a
+ * render loop whose GPU memory budget is fixed at start-up, or a
+ * latency-critical thread where cudaMalloc/cudaFree could stall or implicitly
+ * synchronise the device.  hf_render may allocate (per-slot camera tables,
+ * pinned staging, CUDA graphs) on its first calls or when a batch grows; this
+ * function calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * It renders n <= HF_NOALLOC_MAX_CAMERAS cameras with the same kernel and the
+ * same results as hf_render, always as one batched launch on the context's
+ * own stream (opts->cuda_stream must be NULL or that stream), so edits and
+ * renders stay ordered.  Honoured flags: HF_SHADOWS and HF_SYNC (with HF_SYNC
+ * the step-guard status is returned; without it this entry point reports no
+ * step-guard status, and hf_sync does not see it).  Other flags are ignored.
+ *
+ * Scratch: one statically allocated device array of about 28 KiB (batch
+ * header with the tile counter, camera table, status word) that every GPU
+ * loading this library holds until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) once;
+ * make that first call before any stream capture.  All calls share the array
+ * and it keeps the last call's contents; each call rewrites what must start
+ * at zero.  Calls whose GPU work overlaps (from several threads or contexts on
+ * one device) race on the array; calls ordered on one stream do not.  The
+ * camera table is copied from pageable host memory, so the call waits for
+ * earlier work on the context's stream before returning.
+ * Errors: HF_E_INVALID_ARG (null, n > HF_NOALLOC_MAX_CAMERAS, invalid camera,
+ * tile shape or stream), HF_E_CUDA, and with HF_SYNC HF_E_STEP_LIMIT. */
+#define HF_NOALLOC_MAX_CAMERAS 256u
+int hf_render_noalloc(hf_ctx *ctx, const hf_camera *cams, uint32_t n, const hf_outputs *outs,
+                      const hf_render_opts *opts);
+
 /* Wait for all work the context issued (every render slot and the context
  * stream).  Returns HF_E_STEP_LIMIT if any ray of any render since the last
  * hf_sync hit its step guard (and clears that flag), else HF_OK / HF_E_CUDA. */

@@ -1,7 +1,7 @@
 """Python binding of libhf.so: exact two-interval height-field ray casting on GB300.
 
 A thin ctypes layer over the C ABI in include/hf.h, with the same names:
-``hf_create``, ``hf_edit``, ``hf_render``, ``hf_sync``, ``hf_destroy``,
+``hf_create``, ``hf_edit``, ``hf_render``, ``hf_render_noalloc``, ``hf_sync``, ``hf_destroy``,
 ``hf_camera_from_pose``, ``hf_validate_camera``, ``hf_validate_cells``,
 ``hf_strerror``, ``hf_info``, ``hf_read_cells``, ``hf_read_pyramid``,
 ``hf_rebuild``, ``hf_stats``.  It only marshals arguments: every step of the
@@ -42,6 +42,7 @@ HF_NOWAIT = 32
 HF_MIP_AUTO = 0xFFFFFFFF
 HF_MAX_DIM = 16384
 HF_MAX_CAMERAS = 4096
+HF_NOALLOC_MAX_CAMERAS = 256
 
 
 class HFError(RuntimeError):
@@ -97,6 +98,7 @@ _SIGS = {
     "hf_create": ([ctypes.POINTER(hf_desc), ctypes.POINTER(_P)], ctypes.c_int),
     "hf_edit": ([_P, _U32, _U32, _U32, _U32, _P, ctypes.c_size_t], ctypes.c_int),
     "hf_render": ([_P, _P, _U32, _P, ctypes.POINTER(hf_render_opts)], ctypes.c_int),
+    "hf_render_noalloc": ([_P, _P, _U32, _P, ctypes.POINTER(hf_render_opts)], ctypes.c_int),
     "hf_sync": ([_P], ctypes.c_int),
     "hf_destroy": ([_P], ctypes.c_int),
     "hf_camera_from_pose": ([ctypes.c_double] * 6 + [_U32, _U32, ctypes.POINTER(hf_camera)],
@@ -207,6 +209,19 @@ def hf_render(ctx, cams, outs, opts=None):
     popts = ctypes.byref(opts) if opts is not None else None
     rc = lib.hf_render(ctx, recs.ctypes.data if n else None, n, oarr, popts)
     _check(rc, "hf_render")
+
+
+def hf_render_noalloc(ctx, cams, outs, opts=None):
+    """hf_render without any allocation in the library (at most
+    HF_NOALLOC_MAX_CAMERAS cameras, context stream only; see include/hf.h)."""
+    recs = camera_records(cams)
+    n = len(recs)
+    if len(outs) != n:
+        raise ValueError("one output set per camera")
+    oarr = _outputs_array(outs)
+    popts = ctypes.byref(opts) if opts is not None else None
+    _check(lib.hf_render_noalloc(ctx, recs.ctypes.data if n else None, n, oarr, popts),
+           "hf_render_noalloc")
 
 
 def hf_sync(ctx):

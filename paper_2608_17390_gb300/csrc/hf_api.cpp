@@ -140,6 +140,21 @@ int read_status(hf_ctx *c) {
 
 }  // namespace
 
+namespace hf {
+
+int ctx_view(const hf_ctx *c, CtxView *out) {
+    if (!c || !out) return -1;
+    out->world = c->wd;
+    out->stream = c->stream;
+    out->device = c->device;
+    out->sm_count = c->sm_count;
+    out->occ_shadows[0] = c->occ[0][0];
+    out->occ_shadows[1] = c->occ[1][0];
+    return 0;
+}
+
+}  // namespace hf
+
 extern "C" {
 
 const char *hf_strerror(int code) {

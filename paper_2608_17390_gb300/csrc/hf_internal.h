@@ -10,6 +10,8 @@
 
 #include <cstdint>
 
+struct hf_ctx;  // the C ABI's opaque context (hf_api.cpp)
+
 namespace hf {
 
 constexpr int kMaxLevels = 14;  // 2^14 = 16384 = largest grid side
@@ -68,6 +70,16 @@ int launch_trace_plain(const RenderParams &p, bool shadows, bool stats, uint32_t
                        uint32_t n_tiles, void *stream);
 const void *trace_batched_fn(bool shadows, bool stats);
 int trace_batched_occupancy(bool shadows, bool stats, int *blocks_per_sm);
+
+// What the allocation-free render needs to know about a context (hf_api.cpp).
+struct CtxView {
+    WorldDev world;
+    void *stream;
+    int device;
+    int sm_count;
+    int occ_shadows[2];  // batched-kernel blocks per SM without / with shadow rays
+};
+int ctx_view(const ::hf_ctx *ctx, CtxView *out);
 
 // Pyramid (hf_pyramid.cu): repair the nodes covering cell rectangle
 // [x0, x1) x [y0, y1) at every level 1..L, in order.

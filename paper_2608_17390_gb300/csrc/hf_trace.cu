@@ -19,6 +19,10 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <cstring>
+#include <mutex>
+
+#include "hf.h"
 #include "hf_internal.h"
 
 namespace hf {
@@ -492,3 +496,171 @@ int launch_trace_plain(const RenderParams &p, bool shadows, bool stats, uint32_t
 }
 
 }  // namespace hf
+
+// ------------------------------------------------------------------------
+// Allocation-free render (hf_render_noalloc).  The paper has no counterpart:
+// this exists for callers that must not allocate device memory once they are
+// running (a render thread whose memory budget is fixed at start-up, or a
+// loop where cudaMalloc/cudaFree would stall or implicitly synchronise the
+// device).  hf_render may allocate its per-slot camera tables and CUDA graphs
+// on first use or when a batch grows; this entry point never does.
+//
+// Its scratch -- the batch header with the tile counter, the camera table and
+// the step-guard status word -- is one file-scope device array, present on
+// every GPU that loads this library until the process exits.  Every call
+// shares it and it keeps the last call's contents: each call rewrites the
+// header (tile counter zero) and the camera table, and clears the status word,
+// before its kernel runs.  Two calls whose work overlaps on the GPU race on
+// this array; calls ordered on one stream do not.
+namespace hf {
+namespace {
+
+constexpr size_t kNoallocCamOff = sizeof(BatchHeader);
+constexpr size_t kNoallocStatusOff = kNoallocCamOff + (size_t)HF_NOALLOC_MAX_CAMERAS * sizeof(CamDev);
+constexpr size_t kNoallocBytes = (kNoallocStatusOff + 64 + 255) & ~(size_t)255;
+static_assert(kNoallocStatusOff % 8 == 0, "status words need 8-byte alignment");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device.  In host code the array's name is only a host-side handle.
+int noalloc_scratch(int device, void **out) {
+    if (device < 0 || device >= kMaxDevices) return HF_E_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+            (void)cudaGetLastError();
+            return HF_E_CUDA;
+        }
+        g_noalloc_ptr[device] = ptr;
+    }
+    *out = g_noalloc_ptr[device];
+    return HF_OK;
+}
+
+int ilog2_pow2(uint32_t v) {
+    if (v == 0 || (v & (v - 1))) return -1;
+    int k = 0;
+    while ((1u << k) < v) ++k;
+    return k;
+}
+
+}  // namespace
+}  // namespace hf
+
+extern "C" int hf_render_noalloc(hf_ctx *ctx, const hf_camera *cams, uint32_t n,
+                                 const hf_outputs *outs, const hf_render_opts *opts) {
+    using namespace hf;
+    if (!ctx) return HF_E_INVALID_ARG;
+    if (n == 0) return HF_OK;
+    if (!cams || !outs) return HF_E_INVALID_ARG;
+    if (n > HF_NOALLOC_MAX_CAMERAS) return HF_E_INVALID_ARG;
+    CtxView v;
+    if (ctx_view(ctx, &v)) return HF_E_INVALID_ARG;
+    hf_render_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.mip_start = HF_MIP_AUTO;
+    if (opts) o = *opts;
+    if (o.cuda_stream && o.cuda_stream != v.stream) return HF_E_INVALID_ARG;
+    const uint32_t tw = o.tile_w ? o.tile_w : 8, th = o.tile_h ? o.tile_h : 4;
+    const int twl = ilog2_pow2(tw), thl = ilog2_pow2(th);
+    if (twl < 0 || thl < 0 || tw * th < 32 || tw * th > 256 || tw > 256 || th > 256)
+        return HF_E_INVALID_ARG;
+    int32_t sun[3] = {o.sun[0], o.sun[1], o.sun[2]};
+    if (sun[0] == 0 && sun[1] == 0 && sun[2] == 0) {
+        sun[0] = 321060;
+        sun[1] = -321060;
+        sun[2] = 262144;
+    }
+    for (int i = 0; i < 3; ++i)
+        if (sun[i] <= -(1 << 21) || sun[i] >= (1 << 21)) return HF_E_INVALID_ARG;
+
+    // header + camera table, built on the stack (no allocation)
+    alignas(16) unsigned char buf[kNoallocStatusOff];
+    auto *hdr = reinterpret_cast<BatchHeader *>(buf);
+    std::memset(hdr, 0, sizeof(*hdr));
+    auto *cd = reinterpret_cast<CamDev *>(buf + kNoallocCamOff);
+    uint64_t base = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        const hf_camera &k = cams[i];
+        if (hf_validate_camera((uint32_t)v.world.W, (uint32_t)v.world.H, &k) != HF_OK)
+            return HF_E_INVALID_ARG;
+        CamDev &c = cd[i];
+        for (int a = 0; a < 3; ++a) {
+            c.o[a] = (int32_t)k.origin[a];
+            c.F[a] = k.fwd[a];
+            c.R[a] = k.right[a];
+            c.U[a] = k.up[a];
+        }
+        c.w = k.w;
+        c.h = k.h;
+        c.tiles_x = (k.w + tw - 1) / tw;
+        c.tile_base = (uint32_t)base;
+        base += (uint64_t)c.tiles_x * ((k.h + th - 1) / th);
+        if (base >= 0xFFFFFFFFull) return HF_E_INVALID_ARG;
+        c.hit_cell = outs[i].hit_cell;
+        c.layer = outs[i].layer;
+        c.face = outs[i].face;
+        c.depth = outs[i].depth;
+        c.rgba = outs[i].rgba;
+        c.shadow = outs[i].shadow;
+    }
+    hdr->n_cams = n;
+    hdr->total_tiles = (uint32_t)base;
+
+    if (cudaSetDevice(v.device) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return HF_E_CUDA;
+    }
+    void *scratch = nullptr;
+    int rc = noalloc_scratch(v.device, &scratch);
+    if (rc != HF_OK) return rc;
+    unsigned char *sp = static_cast<unsigned char *>(scratch);
+    cudaStream_t stream = (cudaStream_t)v.stream;
+    const size_t bytes = kNoallocCamOff + (size_t)n * sizeof(CamDev);
+    if (cudaMemcpyAsync(sp, buf, bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+        cudaMemsetAsync(sp + kNoallocStatusOff, 0, 64, stream) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return HF_E_CUDA;
+    }
+    const bool shadows = (o.flags & HF_SHADOWS) != 0;
+    const uint32_t mip = o.mip_start == HF_MIP_AUTO ? 5u : o.mip_start;
+    const uint64_t guard = 4ull * ((uint64_t)v.world.W + (uint64_t)v.world.H) + 64;
+    const uint32_t steps = o.max_steps ? o.max_steps : (uint32_t)guard;
+    if (steps > 0x7FFFFFFFu) return HF_E_INVALID_ARG;
+    RenderParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.world = v.world;
+    p.hdr = reinterpret_cast<BatchHeader *>(sp);
+    p.cams = reinterpret_cast<const CamDev *>(sp + kNoallocCamOff);
+    p.status = reinterpret_cast<uint32_t *>(sp + kNoallocStatusOff);
+    p.stats = reinterpret_cast<unsigned long long *>(sp + kNoallocStatusOff + 8);
+    p.tile_w_log2 = twl;
+    p.tile_h_log2 = thl;
+    p.mip_start = (int32_t)(mip > (uint32_t)v.world.L ? (uint32_t)v.world.L : mip);
+    p.max_steps = (int32_t)steps;
+    const double sn = sqrt((double)sun[0] * sun[0] + (double)sun[1] * sun[1] +
+                           (double)sun[2] * sun[2]);
+    for (int i = 0; i < 3; ++i) {
+        p.sun[i] = sun[i];
+        p.sun_n[i] = (float)(sun[i] / sn);
+    }
+    const int blocks = v.sm_count * v.occ_shadows[shadows ? 1 : 0];
+    if (launch_trace_batched(p, shadows, false, blocks, stream)) return HF_E_CUDA;
+    if (o.flags & HF_SYNC) {
+        uint32_t status = 0;
+        if (cudaMemcpyAsync(&status, p.status, sizeof(status), cudaMemcpyDeviceToHost, stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(stream) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return HF_E_CUDA;
+        }
+        if (status) return HF_E_STEP_LIMIT;
+    }
+    return HF_OK;
+}
