@@ -7,7 +7,9 @@ cameras of the batched-cameras workload (16 x 3840x2160, 24 x 1920x1080,
 the 2048 x 2048 walls-and-caves grid.  value = primary rays / s over all ranks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hf|reference]
-                  [--workload c3|c2|c4|c1]
+                  [--workload c3|c2|c4|c1|c5]
+
+--workload c5 runs the serving loop instead and prints its latency line.
 
 Under torchrun each rank renders its own copy of the batch (weak scaling, no
 data-path collective); rank 0 prints one JSON line.
@@ -184,7 +186,6 @@ def run_hf(args):
     ctx = hf.hf_create(cells, stream=stream.cuda_stream)
     info = hf.hf_info(ctx)
     flags = hf.HF_SHADOWS if wl["shadows"] else 0
-    opts = hf.make_opts(flags=flags, mip_start=args.mip, tile_w=args.tile_w, tile_h=args.tile_h)
 
     def step_cams(i):
         if fps:
@@ -194,6 +195,16 @@ def run_hf(args):
 
     max_cams = step_cams(0)
     outs = hf.alloc_outputs(max_cams, device="cuda", shadows=wl["shadows"])
+    tuned = None
+    if args.mip == 0xFFFFFFFF and not args.tile_w and not args.tile_h and not args.no_tune:
+        from paper_2608_17390_gb300.autotune import autotune
+
+        opts, table = autotune(ctx, max_cams, outs, stream, shadows=wl["shadows"], reps=2)
+        tuned = {"candidates": len(table), "best_ms": min(r[3] for r in table) if table else None}
+    else:
+        opts = hf.make_opts(flags=flags, mip_start=args.mip, tile_w=args.tile_w,
+                            tile_h=args.tile_h)
+    tile_w, tile_h, mip_start = opts.tile_w or 8, opts.tile_h or 4, opts.mip_start
     rng = np.random.default_rng(1234 + rank)
     H, W = cells.shape
 
@@ -220,8 +231,8 @@ def run_hf(args):
             rec[2].record(stream)
 
     # untimed: fetch counters for the algorithmic bytes of one render
-    sopts = hf.make_opts(flags=flags | hf.HF_STATS, mip_start=args.mip, tile_w=args.tile_w,
-                         tile_h=args.tile_h)
+    sopts = hf.make_opts(flags=flags | hf.HF_STATS, mip_start=mip_start, tile_w=tile_w,
+                         tile_h=tile_h)
     hf.hf_stats(ctx)
     hf.hf_render(ctx, max_cams, outs[:len(max_cams)], sopts)
     st = hf.hf_stats(ctx)
@@ -260,8 +271,8 @@ def run_hf(args):
     # plain: one launch per camera, same accuracy, same stream, L2 flushed
     plain = None
     if not args.no_plain:
-        popts = hf.make_opts(flags=flags | hf.HF_PLAIN, mip_start=args.mip, tile_w=args.tile_w,
-                             tile_h=args.tile_h)
+        popts = hf.make_opts(flags=flags | hf.HF_PLAIN, mip_start=mip_start, tile_w=tile_w,
+                             tile_h=tile_h)
         pms = []
         for i in range(max(1, min(3, args.steps))):
             with torch.cuda.stream(stream):
@@ -327,8 +338,9 @@ def run_hf(args):
         "data": "synthetic (seeded value-noise terrain standing in for the paper's Fostral level)",
         "config": {"workload": wl["name"], "rays_per_step": int(rays_step),
                    "grid": "%dx%d" % (W, H), "l2": "flushed between steps (256 MiB write)",
-                   "mip_start": "auto" if args.mip == 0xFFFFFFFF else args.mip,
-                   "tile": "%dx%d" % (args.tile_w or 8, args.tile_h or 4),
+                   "mip_start": "library default" if mip_start == 0xFFFFFFFF else mip_start,
+                   "tile": "%dx%d" % (tile_w, tile_h),
+                   "autotuned": tuned,
                    "world_bytes": info["cell_bytes"] + info["pyramid_bytes"]},
         "plain_rays_per_s": plain,
         "batched_over_plain": (value / ws / plain) if plain else None,
@@ -352,6 +364,69 @@ def run_hf(args):
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+def run_serve(args):
+    """Serving loop on the large world: p50/p99 frame and edit-to-visible
+    latency at ~70 % and ~100 % of the measured batched capacity."""
+    import torch
+
+    import __graft_entry__
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local if ws > 1 else 0)
+    __graft_entry__.build_library()
+    import paper_2608_17390_gb300 as hf
+    from paper_2608_17390_gb300 import serve
+    import synth
+
+    cells = synth.config_c4()["cells"]
+    srv = serve.Server(cells, lanes=4, mem_bytes=4 << 30, max_batch=32)
+    # capacity: one batched render of 64 representative requests
+    probe = [r for r in synth.poisson_requests(cells, 72, 1.0, seed=99) if r["kind"] == "render"]
+    cams = np.array([r["cam"] for r in probe])
+    outs = hf.alloc_outputs(cams)
+    ms = []
+    for _ in range(4):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(srv.main)
+        hf.hf_render(srv.ctx, cams, outs, hf.make_opts(stream=srv.main.cuda_stream))
+        b.record(srv.main)
+        hf.hf_sync(srv.ctx)
+        ms.append(a.elapsed_time(b))
+    cap_rays = n_rays(cams) / (float(np.median(ms[1:])) / 1e3)
+    mean_rays = n_rays(cams) / len(cams)
+    cap_req = cap_rays / mean_rays * 10.0 / 11.0  # requests/s incl. 1 edit per 10 renders
+    del outs
+    results = {}
+    for load in (0.7, 1.0):
+        reqs = serve.requests_from(synth.poisson_requests(cells, args.serve_requests,
+                                                          load * cap_req, seed=int(load * 100)))
+        t0 = time.perf_counter()
+        done = srv.run(reqs)
+        wall = time.perf_counter() - t0
+        st = serve.summarize(done, wall)
+        st["offered_requests_per_s"] = load * cap_req
+        st["batches"] = srv.batches
+        st["max_inflight_batches"] = srv.max_inflight
+        results["load_%d%%" % int(load * 100)] = st
+    srv.close()
+    if rank != 0:
+        return
+    hi = results["load_100%"]
+    line = {"metric": "p50/p99 frame and edit-to-visible latency, serving loop (continuous "
+                      "batching, 10 renders : 1 edit)",
+            "value": hi["frame_ms_p99"], "unit": "ms (p99 frame latency at ~100% load)",
+            "n_gpus": ws, "steps": args.serve_requests, "warmup": 0,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+            "data": "synthetic",
+            "config": {"workload": "C5 serving: 2048x16384 grid resident, Poisson render "
+                                   "requests (640x360..3840x2160, random poses) with a 64x64 "
+                                   "crater edit every 11th request", "lanes": 4,
+                       "output_memory_budget_bytes": 4 << 30, "max_batch": 32},
+            "capacity_rays_per_s": cap_rays, "capacity_requests_per_s": cap_req,
+            "loads": results}
+    print(json.dumps(line))
 
 
 def run_reference(args):
@@ -385,7 +460,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hf", choices=["hf", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4"])
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--serve-requests", type=int, default=2200)
     ap.add_argument("--mip", type=int, default=0xFFFFFFFF)
     ap.add_argument("--tile-w", type=int, default=0)
     ap.add_argument("--tile-h", type=int, default=0)
@@ -395,11 +471,14 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "hf":
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "c5":
+        run_serve(args)
     else:
         run_hf(args)
 

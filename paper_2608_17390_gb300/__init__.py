@@ -137,11 +137,17 @@ def hf_strerror(code):
     return lib.hf_strerror(int(code)).decode()
 
 
+_CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy: the legacy default stream's handle
+
+
 def _current_stream():
+    """torch's current stream as a cudaStream_t; its default stream (handle 0)
+    is passed as cudaStreamLegacy so that the library orders its work on it
+    instead of creating a stream of its own."""
     try:
         import torch
         if torch.cuda.is_available():
-            return torch.cuda.current_stream().cuda_stream
+            return torch.cuda.current_stream().cuda_stream or _CUDA_STREAM_LEGACY
     except ImportError:
         pass
     return None

@@ -27,7 +27,6 @@ constexpr size_t kScratchAlign = 4096;
 constexpr int kMaxGraphsPerSlot = 16;
 constexpr int32_t kLimit21 = 1 << 21;
 constexpr int32_t kDefaultSun[3] = {321060, -321060, 262144};
-constexpr uint32_t kDefaultMip = 5;
 
 struct GraphKey {
     uint32_t bytes, shadows, stats, twl, thl, mip, steps;
@@ -556,7 +555,7 @@ int hf_render(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_outputs *ou
     if (total_tiles >= 0xFFFFFFFFull) return HF_E_INVALID_ARG;
     const bool shadows = (o.flags & HF_SHADOWS) != 0;
     const bool stats = (o.flags & HF_STATS) != 0;
-    const uint32_t mip = o.mip_start == HF_MIP_AUTO ? kDefaultMip : o.mip_start;
+    const uint32_t mip = o.mip_start == HF_MIP_AUTO ? hf::kDefaultMipStart : o.mip_start;
     const uint32_t mip_c = mip > c->L ? c->L : mip;
     const uint64_t guard = 4ull * (c->W + c->H) + 64;
     const uint32_t steps = o.max_steps ? o.max_steps : (uint32_t)(guard > 0x7FFFFFFF ? 0x7FFFFFFF : guard);

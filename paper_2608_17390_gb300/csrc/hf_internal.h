@@ -18,6 +18,7 @@ constexpr int kMaxLevels = 14;  // 2^14 = 16384 = largest grid side
 constexpr int kShift = 16;      // 2^16 fixed-point units per world unit
 constexpr int kThreads = 128;   // threads per trace block (4 warps)
 constexpr uint32_t kMaxCams = 4096;
+constexpr uint32_t kDefaultMipStart = 6;  // coarsest level used when the caller asks for the default
 
 constexpr uint8_t kFaceNX = 0, kFacePX = 1, kFaceNY = 2, kFacePY = 3, kFaceNZ = 4, kFacePZ = 5,
                   kFaceInside = 6, kFaceError = 254, kFaceMiss = 255;

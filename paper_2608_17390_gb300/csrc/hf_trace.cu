@@ -28,6 +28,10 @@
 namespace hf {
 namespace {
 
+#ifndef HF_TRACE_MIN_BLOCKS
+#define HF_TRACE_MIN_BLOCKS 6  // resident blocks per SM asked of the register allocator (<= 80 registers)
+#endif
+
 __constant__ float c_albedo[8][3] = {
     {0.55f, 0.50f, 0.40f}, {0.35f, 0.55f, 0.25f}, {0.60f, 0.60f, 0.62f}, {0.80f, 0.72f, 0.50f},
     {0.30f, 0.30f, 0.32f}, {0.70f, 0.35f, 0.20f}, {0.90f, 0.90f, 0.95f}, {0.25f, 0.40f, 0.60f},
@@ -69,14 +73,30 @@ __device__ __forceinline__ int32_t floor_quot(int64_t Q, int32_t a, float rcp_a,
     return q;
 }
 
-__device__ __forceinline__ int64_t floor_div64(int64_t a, int32_t b) {  // b > 0
-    int64_t q = a / b;
-    if ((a % b) != 0 && a < 0) q -= 1;
+// floor(a / b) for |a| < 2^52, 0 < b < 2^21 and |a / b| < 2^30: a float
+// estimate, a second estimate from the remainder, then one exact correction.
+__device__ __forceinline__ int32_t floor_div_small(int64_t a, int32_t b, float rcp_b) {
+    int32_t q = (int32_t)floorf((float)a * rcp_b);             // within ~2^9 of the quotient
+    int64_t r = a - (int64_t)q * b;                            // |r| < 2^31
+    q += (int32_t)floorf((float)r * rcp_b);                    // within 1
+    r = a - (int64_t)q * b;
+    if (r < 0) q -= 1;
+    else if (r >= b) q += 1;
     return q;
 }
 
 __device__ __forceinline__ uint32_t load_word(const WorldDev &w, int level, int32_t x, int32_t y) {
     return __ldg(w.base + w.off[level] + (uint32_t)y * w.stride[level] + (uint32_t)x);
+}
+
+// A cell word in pyramid-node form: max h0, min (slab ? h1 : 255), max top.
+// For one cell the node emptiness test is exact: the segment's z range
+// [zlo, zhi] misses (-inf, h0] and [h1, h2] exactly when zlo > top, or
+// zlo > h0 and zhi < h1.
+__device__ __forceinline__ uint32_t cell_as_node(uint32_t c) {
+    const uint32_t h0 = c & 0xFF, h1 = (c >> 8) & 0xFF, h2 = (c >> 16) & 0xFF;
+    const bool slab = h1 > h0;
+    return h0 | ((slab ? h1 : 255u) << 8) | ((slab ? h2 : h0) << 16);
 }
 
 // The two-interval test of one cell over [tin, tout] (tout finite).
@@ -212,24 +232,25 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const Ray &r, int m
         const int32_t tout_num = xfirst ? numx : numy;
         const int32_t tout_den = xfirst ? adx : ady;
         const uint32_t word = load_word(w, level, nx, ny);
-
-        if (level > 0) {
-            if (STATS) cnt.nodes++;
-            const int32_t maxh0 = word & 0xFF, minh1 = (word >> 8) & 0xFF,
-                          maxtop = (word >> 16) & 0xFF;
-            const bool down = r.dz < 0;
-            const int32_t lo_num = down ? tout_num : tin_num, lo_den = down ? tout_den : tin_den;
-            const int32_t hi_num = down ? tin_num : tout_num, hi_den = down ? tin_den : tout_den;
-            const bool empty =
-                zd(r.oz - (maxtop << kShift), r.dz, lo_num, lo_den) > 0 ||
-                (zd(r.oz - (maxh0 << kShift), r.dz, lo_num, lo_den) > 0 &&
-                 zd(r.oz - (minh1 << kShift), r.dz, hi_num, hi_den) < 0);
-            if (!empty) {
+        const uint32_t node = level > 0 ? word : cell_as_node(word);
+        if (STATS) {
+            if (level > 0) cnt.nodes++;
+            else cnt.cells++;
+        }
+        const int32_t maxh0 = node & 0xFF, minh1 = (node >> 8) & 0xFF,
+                      maxtop = (node >> 16) & 0xFF;
+        const bool down = r.dz < 0;
+        const int32_t lo_num = down ? tout_num : tin_num, lo_den = down ? tout_den : tin_den;
+        const int32_t hi_num = down ? tin_num : tout_num, hi_den = down ? tin_den : tout_den;
+        const bool empty = zd(r.oz - (maxtop << kShift), r.dz, lo_num, lo_den) > 0 ||
+                           (zd(r.oz - (maxh0 << kShift), r.dz, lo_num, lo_den) > 0 &&
+                            zd(r.oz - (minh1 << kShift), r.dz, hi_num, hi_den) < 0);
+        if (!empty) {
+            if (level > 0) {
                 --level;
                 continue;
             }
-        } else {
-            if (STATS) cnt.cells++;
+            // a non-empty cell holds the hit: find its layer, face and time
             if (leaf_test(r, word, tin_num, tin_den, tout_num, tout_den, entry, h)) {
                 h.cx = cx;
                 h.cy = cy;
@@ -321,57 +342,67 @@ __device__ __forceinline__ void trace_pixel(const RenderParams &p, const CamDev 
     r.dx = c.F[0] + a * c.R[0] + b * c.U[0];
     r.dy = c.F[1] + a * c.R[1] + b * c.U[1];
     r.dz = c.F[2] + a * c.R[2] + b * c.U[2];
-    Hit h;
-    trace_ray<STATS>(p.world, r, p.mip_start, p.max_steps, h, cnt);
-    const uint32_t pix = (uint32_t)py * c.w + (uint32_t)px;
-    const bool hit = h.face < kFaceError;
-    if (h.face == kFaceError) err = true;
+    // primary hit, kept while the shadow ray reuses the traversal loop
+    Hit ph;
+    float depth = __int_as_float(0x7f800000);
     bool visible = true;
-    if (SHADOWS && hit) {
-        if (h.face == kFaceInside) {
-            visible = false;
+    bool shadow_pass = false;
+    for (;;) {
+        Hit h;
+        if (!SHADOWS || !shadow_pass) {
+            trace_ray<STATS>(p.world, r, p.mip_start, p.max_steps, h, cnt);
         } else {
-            Ray s;
-            int64_t px64 = (int64_t)r.ox + floor_div64((int64_t)h.tnum * r.dx, h.tden);
-            int64_t py64 = (int64_t)r.oy + floor_div64((int64_t)h.tnum * r.dy, h.tden);
-            int64_t pz64 = (int64_t)r.oz + floor_div64((int64_t)h.tnum * r.dz, h.tden);
-            switch (h.face) {
-                case kFaceNX: px64 -= 1; break;
-                case kFacePX: px64 += 1; break;
-                case kFaceNY: py64 -= 1; break;
-                case kFacePY: py64 += 1; break;
-                case kFaceNZ: pz64 -= 1; break;
-                default: pz64 += 1; break;
-            }
-            s.ox = (int32_t)px64;
-            s.oy = (int32_t)py64;
-            s.oz = (int32_t)pz64;
-            s.dx = p.sun[0];
-            s.dy = p.sun[1];
-            s.dz = p.sun[2];
-            Hit sh;
-            if (STATS) nshadow++;
-            if (px64 >= 0 && py64 >= 0) {
-                trace_ray<STATS>(p.world, s, p.mip_start, p.max_steps, sh, scnt);
-                if (sh.face == kFaceError) err = true;
-                visible = sh.face == kFaceMiss;
-            }
+            trace_ray<STATS>(p.world, r, p.mip_start, p.max_steps, h, scnt);
         }
-    }
-    if (SHADOWS && c.shadow) __stcs(c.shadow + pix, (uint8_t)(visible ? 0 : 1));
-    if (c.hit_cell) __stcs(c.hit_cell + pix, hit ? (uint32_t)h.cy * (uint32_t)p.world.W + (uint32_t)h.cx : 0xFFFFFFFFu);
-    if (c.layer) __stcs(c.layer + pix, hit ? h.layer : (uint8_t)255);
-    if (c.face) __stcs(c.face + pix, h.face);
-    if (c.depth) {
-        float dep = __int_as_float(0x7f800000);
+        if (h.face == kFaceError) err = true;
+        if (SHADOWS && shadow_pass) {
+            visible = h.face == kFaceMiss;
+            break;
+        }
+        ph = h;
+        const bool hit = h.face < kFaceError;
         if (hit) {
             const float fx = (float)r.dx, fy = (float)r.dy, fz = (float)r.dz;
-            const float n = sqrtf(fx * fx + fy * fy + fz * fz);
-            dep = ((float)h.tnum / (float)h.tden) * n * (1.0f / 65536.0f);
+            depth = ((float)h.tnum / (float)h.tden) * sqrtf(fx * fx + fy * fy + fz * fz) *
+                    (1.0f / 65536.0f);
         }
-        __stcs(c.depth + pix, dep);
+        if (!SHADOWS || !hit) break;
+        if (h.face == kFaceInside) {
+            visible = false;
+            break;
+        }
+        // shadow ray: floor of the hit point, one unit outward along the face normal
+        const float rcp_t = 1.0f / (float)h.tden;
+        int32_t sxp = r.ox + floor_div_small((int64_t)h.tnum * r.dx, h.tden, rcp_t);
+        int32_t syp = r.oy + floor_div_small((int64_t)h.tnum * r.dy, h.tden, rcp_t);
+        int32_t szp = r.oz + floor_div_small((int64_t)h.tnum * r.dz, h.tden, rcp_t);
+        switch (h.face) {
+            case kFaceNX: sxp -= 1; break;
+            case kFacePX: sxp += 1; break;
+            case kFaceNY: syp -= 1; break;
+            case kFacePY: syp += 1; break;
+            case kFaceNZ: szp -= 1; break;
+            default: szp += 1; break;
+        }
+        r.ox = sxp;
+        r.oy = syp;
+        r.oz = szp;
+        r.dx = p.sun[0];
+        r.dy = p.sun[1];
+        r.dz = p.sun[2];
+        if (STATS) nshadow++;
+        shadow_pass = true;
     }
-    if (c.rgba) __stcs(c.rgba + pix, hit ? shade(h.word, h.face, visible, p.sun_n) : kSky);
+    const uint32_t pix = (uint32_t)py * c.w + (uint32_t)px;
+    const bool hit = ph.face < kFaceError;
+    if (SHADOWS && c.shadow) __stcs(c.shadow + pix, (uint8_t)(visible ? 0 : 1));
+    if (c.hit_cell)
+        __stcs(c.hit_cell + pix,
+               hit ? (uint32_t)ph.cy * (uint32_t)p.world.W + (uint32_t)ph.cx : 0xFFFFFFFFu);
+    if (c.layer) __stcs(c.layer + pix, hit ? ph.layer : (uint8_t)255);
+    if (c.face) __stcs(c.face + pix, ph.face);
+    if (c.depth) __stcs(c.depth + pix, depth);
+    if (c.rgba) __stcs(c.rgba + pix, hit ? shade(ph.word, ph.face, visible, p.sun_n) : kSky);
 }
 
 template <bool SHADOWS, bool STATS>
@@ -409,13 +440,25 @@ __device__ __forceinline__ void trace_tile(const RenderParams &p, const CamDev &
     }
 }
 
-__device__ __forceinline__ CamDev load_cam(const CamDev *cams, uint32_t i) { return cams[i]; }
+// Copy camera i into this warp's shared slot (fields are then read on demand
+// instead of being held in registers for the whole tile).
+__device__ __forceinline__ const CamDev &stage_cam(CamDev *slot, const CamDev *cams, uint32_t i,
+                                                   int lane) {
+    static_assert(sizeof(CamDev) % 4 == 0 && sizeof(CamDev) / 4 <= 32, "one word per lane");
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(cams + i);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(slot);
+    __syncwarp();
+    if (lane < (int)(sizeof(CamDev) / 4)) dst[lane] = src[lane];
+    __syncwarp();
+    return *slot;
+}
 
 // Persistent batched kernel: warps pop (camera, tile) items from one atomic
 // counter until the batch is drained.  One launch renders every camera.
 template <bool SHADOWS, bool STATS>
-__global__ void __launch_bounds__(kThreads) k_trace_batched(const RenderParams p) {
+__global__ void __launch_bounds__(kThreads, HF_TRACE_MIN_BLOCKS) k_trace_batched(const RenderParams p) {
     __shared__ uint32_t s_base[kMaxCams + 1];
+    __shared__ CamDev s_cam[kThreads / 32];
     const uint32_t n = p.hdr->n_cams;
     const uint32_t total = p.hdr->total_tiles;
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) s_base[i] = p.cams[i].tile_base;
@@ -433,19 +476,21 @@ __global__ void __launch_bounds__(kThreads) k_trace_batched(const RenderParams p
             if (s_base[mid] <= t) lo = mid;
             else hi = mid;
         }
-        const CamDev c = load_cam(p.cams, lo);
+        const CamDev &c = stage_cam(&s_cam[threadIdx.x >> 5], p.cams, lo, lane);
         trace_tile<SHADOWS, STATS>(p, c, t - s_base[lo], lane);
     }
 }
 
 // Plain kernel: one camera, one warp per tile, grid covers the image once.
 template <bool SHADOWS, bool STATS>
-__global__ void __launch_bounds__(kThreads) k_trace_plain(const RenderParams p, uint32_t cam,
+__global__ void __launch_bounds__(kThreads, HF_TRACE_MIN_BLOCKS) k_trace_plain(const RenderParams p, uint32_t cam,
                                                           uint32_t n_tiles) {
+    __shared__ CamDev s_cam[kThreads / 32];
     const uint32_t t = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
     if (t >= n_tiles) return;
-    const CamDev c = load_cam(p.cams, cam);
-    trace_tile<SHADOWS, STATS>(p, c, t, threadIdx.x & 31);
+    const int lane = threadIdx.x & 31;
+    const CamDev &c = stage_cam(&s_cam[threadIdx.x >> 5], p.cams, cam, lane);
+    trace_tile<SHADOWS, STATS>(p, c, t, lane);
 }
 
 template <bool SH, bool ST>
@@ -629,7 +674,7 @@ extern "C" int hf_render_noalloc(hf_ctx *ctx, const hf_camera *cams, uint32_t n,
         return HF_E_CUDA;
     }
     const bool shadows = (o.flags & HF_SHADOWS) != 0;
-    const uint32_t mip = o.mip_start == HF_MIP_AUTO ? 5u : o.mip_start;
+    const uint32_t mip = o.mip_start == HF_MIP_AUTO ? kDefaultMipStart : o.mip_start;
     const uint64_t guard = 4ull * ((uint64_t)v.world.W + (uint64_t)v.world.H) + 64;
     const uint32_t steps = o.max_steps ? o.max_steps : (uint32_t)guard;
     if (steps > 0x7FFFFFFFu) return HF_E_INVALID_ARG;

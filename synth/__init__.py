@@ -39,11 +39,13 @@ from .cameras import (
     small_c2,
 )
 
+from .requests import poisson_requests, SERVING_RESOLUTIONS
+
 __all__ = [
     "mix64", "unit_float", "uniform_int",
     "value_noise", "make_grid", "pack_cells", "unpack_cells", "grid_hash",
     "crater_edit",
     "CAMERA_DTYPE", "pose_to_camera", "ray_camera", "camera_array",
     "config_c1", "config_c2", "config_c3", "c3_cameras", "config_c4", "config_c4_frames",
-    "small_c2",
+    "small_c2", "poisson_requests", "SERVING_RESOLUTIONS",
 ]
