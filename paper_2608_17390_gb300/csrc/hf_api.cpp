@@ -271,6 +271,7 @@ static int create_impl(const hf_desc *d, hf_ctx *c) {
         const uint32_t wk = (c->W + (1u << k) - 1) >> k, hk = (c->H + (1u << k) - 1) >> k;
         c->wd.off[k] = (uint32_t)off;
         c->wd.stride[k] = wk;
+        c->wd.rows[k] = hk;
         off += ((size_t)wk * hk + 63) & ~(size_t)63;
     }
     c->world_words = off;
@@ -611,6 +612,7 @@ int hf_render(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_outputs *ou
     p.tile_w_log2 = twl;
     p.tile_h_log2 = thl;
     p.mip_start = (int32_t)mip_c;
+    p.shadow_mip = (int32_t)(mip_c + hf::kShadowMipExtra > c->L ? c->L : mip_c + hf::kShadowMipExtra);
     p.max_steps = (int32_t)steps;
     const double sn = std::sqrt((double)sun[0] * sun[0] + (double)sun[1] * sun[1] +
                                 (double)sun[2] * sun[2]);

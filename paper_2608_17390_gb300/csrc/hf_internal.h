@@ -19,6 +19,11 @@ constexpr int kShift = 16;      // 2^16 fixed-point units per world unit
 constexpr int kThreads = 128;   // threads per trace block (4 warps)
 constexpr uint32_t kMaxCams = 4096;
 constexpr uint32_t kDefaultMipStart = 6;  // coarsest level used when the caller asks for the default
+#ifndef HF_SHADOW_MIP_EXTRA
+#define HF_SHADOW_MIP_EXTRA 0
+#endif
+// shadow rays start this many levels higher (they rise above the terrain and travel far)
+constexpr uint32_t kShadowMipExtra = HF_SHADOW_MIP_EXTRA;
 
 constexpr uint8_t kFaceNX = 0, kFacePX = 1, kFaceNY = 2, kFacePY = 3, kFaceNZ = 4, kFacePZ = 5,
                   kFaceInside = 6, kFaceError = 254, kFaceMiss = 255;
@@ -26,7 +31,8 @@ constexpr uint8_t kFaceNX = 0, kFacePX = 1, kFaceNY = 2, kFacePY = 3, kFaceNZ = 
 struct WorldDev {
     const uint32_t *base;               // level 0 at base, level k at base + off[k]
     uint32_t off[kMaxLevels + 1];       // word offset of each level
-    uint32_t stride[kMaxLevels + 1];    // words per row of each level
+    uint32_t stride[kMaxLevels + 1];    // words per row of each level (= its width in nodes)
+    uint32_t rows[kMaxLevels + 1];      // rows of each level (= its height in nodes)
     int32_t W, H, L;                    // grid size, top level
 };
 
@@ -58,7 +64,8 @@ struct RenderParams {
     uint32_t *status;              // bit 0: a ray hit its step guard
     unsigned long long *stats;     // 5 counters (HF_STATS)
     int32_t tile_w_log2, tile_h_log2;
-    int32_t mip_start;
+    int32_t mip_start;             // coarsest level for primary rays
+    int32_t shadow_mip;            // coarsest level for shadow rays
     int32_t max_steps;
     int32_t sun[3];
     float sun_n[3];                // sun / |sun|

@@ -59,27 +59,19 @@ __device__ __forceinline__ int64_t zd(int32_t oz_minus_hs, int32_t dz, int32_t n
     return (int64_t)oz_minus_hs * den + (int64_t)num * dz;
 }
 
-// floor(Q / a) for 0 <= Q < 2^36, 1 <= a < 2^21, quotient < 2^15; r = remainder.
-__device__ __forceinline__ int32_t floor_quot(int64_t Q, int32_t a, float rcp_a, int64_t &r) {
-    int32_t q = (int32_t)((float)Q * rcp_a);
-    r = Q - (int64_t)q * a;
-    if (r < 0) {
-        q -= 1;
-        r += a;
-    } else if (r >= a) {
-        q += 1;
-        r -= a;
-    }
-    return q;
+// int64 -> float through two 32-bit conversions (64-bit integer conversions
+// run on the FP64 pipe, which is narrow on this GPU).  |v| < 2^52.
+__device__ __forceinline__ float i64_to_f32(int64_t v) {
+    return fmaf((float)(int32_t)(v >> 32), 4294967296.0f, (float)(uint32_t)v);
 }
 
 // floor(a / b) for |a| < 2^52, 0 < b < 2^21 and |a / b| < 2^30: a float
 // estimate, a second estimate from the remainder, then one exact correction.
 __device__ __forceinline__ int32_t floor_div_small(int64_t a, int32_t b, float rcp_b) {
-    int32_t q = (int32_t)floorf((float)a * rcp_b);             // within ~2^9 of the quotient
-    int64_t r = a - (int64_t)q * b;                            // |r| < 2^31
-    q += (int32_t)floorf((float)r * rcp_b);                    // within 1
-    r = a - (int64_t)q * b;
+    int32_t q = (int32_t)floorf(i64_to_f32(a) * rcp_b);        // within ~2^9 of the quotient
+    const int32_t r1 = (int32_t)(a - (int64_t)q * b);          // |r1| < 2^31
+    q += (int32_t)floorf((float)r1 * rcp_b);                   // within 1
+    const int64_t r = a - (int64_t)q * b;
     if (r < 0) q -= 1;
     else if (r >= b) q += 1;
     return q;
@@ -192,6 +184,15 @@ __device__ __forceinline__ bool vertical_test(const Ray &r, uint32_t word, Hit &
 
 // Exact first hit of one ray.  h.face = kFaceMiss on a miss, kFaceError when
 // max_steps iterations did not finish the ray.
+//
+// State: the node (nx, ny) at `level` that holds the ray just after t_in.
+// Skipping an empty node changes only the node index on the exit axis; the
+// finer bits on the other axis are found when the traversal descends, by
+// asking whether the ray has crossed the child midline by t_in (exact
+// cross-multiplied time comparison).  Every interior cell boundary of a node
+// is the midline of exactly one sub-level, so a ray that enters a cell through
+// its Y side while also crossing an X cell boundary (a corner) is detected on
+// the way down and reported with the X face.
 template <bool STATS>
 __device__ __forceinline__ void trace_ray(const WorldDev &w, const Ray &r, int mip_start,
                                           int max_steps, Hit &h, Counters &cnt) {
@@ -215,14 +216,12 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const Ray &r, int m
         return;
     }
 
-    const float rcpx = adx ? 1.0f / (float)adx : 0.0f;
-    const float rcpy = ady ? 1.0f / (float)ady : 0.0f;
+    int level = mip_start;
+    int32_t nx = cx >> level, ny = cy >> level;
     int32_t tin_num = 0, tin_den = 1;
     uint8_t entry = kFaceInside;
-    int level = mip_start;
 
     for (int it = 0; it < max_steps; ++it) {
-        const int32_t nx = cx >> level, ny = cy >> level;
         const int32_t bx = (sx > 0 ? nx + 1 : nx) << level;  // exit boundary (cells)
         const int32_t by = (sy > 0 ? ny + 1 : ny) << level;
         const int32_t numx = sx > 0 ? (bx << kShift) - r.ox : (sx < 0 ? r.ox - (bx << kShift) : 1);
@@ -247,59 +246,63 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const Ray &r, int m
                             zd(r.oz - (minh1 << kShift), r.dz, hi_num, hi_den) < 0);
         if (!empty) {
             if (level > 0) {
+                // descend into the child that holds the ray just after t_in
                 --level;
+                const int32_t xm = (2 * nx + 1) << level, ym = (2 * ny + 1) << level;
+                bool on_x = false;
+                if (sx != 0) {
+                    const int64_t lhs =
+                        (int64_t)(sx > 0 ? (xm << kShift) - r.ox : r.ox - (xm << kShift)) * tin_den;
+                    const int64_t rhs = (int64_t)tin_num * adx;
+                    const bool past = lhs <= rhs;
+                    on_x = lhs == rhs;
+                    nx = 2 * nx + ((sx > 0) == past ? 1 : 0);
+                } else {
+                    nx = 2 * nx + (r.ox >= (xm << kShift) ? 1 : 0);
+                }
+                if (sy != 0) {
+                    const int64_t lhs =
+                        (int64_t)(sy > 0 ? (ym << kShift) - r.oy : r.oy - (ym << kShift)) * tin_den;
+                    const bool past = lhs <= (int64_t)tin_num * ady;
+                    ny = 2 * ny + ((sy > 0) == past ? 1 : 0);
+                } else {
+                    ny = 2 * ny + (r.oy >= (ym << kShift) ? 1 : 0);
+                }
+                if (on_x && (entry == kFaceNY || entry == kFacePY))
+                    entry = sx > 0 ? kFaceNX : kFacePX;  // a corner: report the X face
+                if ((uint32_t)nx >= w.stride[level] || (uint32_t)ny >= w.rows[level]) return;
                 continue;
             }
             // a non-empty cell holds the hit: find its layer, face and time
             if (leaf_test(r, word, tin_num, tin_den, tout_num, tout_den, entry, h)) {
-                h.cx = cx;
-                h.cy = cy;
+                h.cx = nx;
+                h.cy = ny;
                 h.word = word;
                 return;
             }
         }
-
         // advance past the node (or cell) through its exit side
-        int32_t ncx = cx, ncy = cy;
-        bool corner = false;
         if (cmp < 0) {
-            ncx = sx > 0 ? bx : bx - 1;
-            if (level > 0) {
-                const int32_t y0 = ny << level;
-                const int64_t E = (int64_t)(r.oy - (y0 << kShift)) * adx + (int64_t)numx * r.dy;
-                int64_t rem;
-                const int32_t q = floor_quot(E >> kShift, adx, rcpx, rem);
-                const bool exact = ((E & 0xFFFF) == 0) && rem == 0;
-                ncy = y0 + q - ((sy < 0 && exact) ? 1 : 0);
-            }
+            nx += sx;
             entry = sx > 0 ? kFaceNX : kFacePX;
         } else if (cmp > 0) {
-            ncy = sy > 0 ? by : by - 1;
-            if (level > 0) {
-                const int32_t x0 = nx << level;
-                const int64_t E = (int64_t)(r.ox - (x0 << kShift)) * ady + (int64_t)numy * r.dx;
-                int64_t rem;
-                const int32_t q = floor_quot(E >> kShift, ady, rcpy, rem);
-                const bool exact = ((E & 0xFFFF) == 0) && rem == 0;
-                ncx = x0 + q - ((sx < 0 && exact) ? 1 : 0);
-                // x lands exactly on a cell boundary while moving in x: the
-                // cell-level walk crosses a corner here, whose entry face is X
-                corner = exact && sx != 0;
-            }
-            entry = corner ? (sx > 0 ? kFaceNX : kFacePX) : (sy > 0 ? kFaceNY : kFacePY);
+            ny += sy;
+            entry = sy > 0 ? kFaceNY : kFacePY;
         } else {  // exact corner: both axes change
-            ncx = sx > 0 ? bx : bx - 1;
-            ncy = sy > 0 ? by : by - 1;
+            nx += sx;
+            ny += sy;
             entry = sx > 0 ? kFaceNX : kFacePX;
         }
-        cx = ncx;
-        cy = ncy;
         tin_num = tout_num;
         tin_den = tout_den;
-        if ((uint32_t)cx >= (uint32_t)w.W || (uint32_t)cy >= (uint32_t)w.H) return;
+        if ((uint32_t)nx >= w.stride[level] || (uint32_t)ny >= w.rows[level]) return;
         if (level < mip_start) {  // ascend when the crossed boundary is a parent boundary
             const int32_t bnd = cmp <= 0 ? bx : by;
-            if ((bnd & ((2 << level) - 1)) == 0) ++level;
+            if ((bnd & ((2 << level) - 1)) == 0) {
+                ++level;
+                nx >>= 1;
+                ny >>= 1;
+            }
         }
     }
     h.face = kFaceError;
@@ -329,6 +332,23 @@ __device__ __forceinline__ uint32_t shade(uint32_t word, uint8_t face, bool visi
     return out;
 }
 
+// Writes one pixel's outputs.
+__device__ __forceinline__ void store_pixel(const RenderParams &p, const CamDev &c, uint32_t pix,
+                                            const Hit &ph, float depth, bool visible,
+                                            bool shadows) {
+    const bool hit = ph.face < kFaceError;
+    if (shadows && c.shadow) __stcs(c.shadow + pix, (uint8_t)(visible ? 0 : 1));
+    if (c.hit_cell)
+        __stcs(c.hit_cell + pix,
+               hit ? (uint32_t)ph.cy * (uint32_t)p.world.W + (uint32_t)ph.cx : 0xFFFFFFFFu);
+    if (c.layer) __stcs(c.layer + pix, hit ? ph.layer : (uint8_t)255);
+    if (c.face) __stcs(c.face + pix, ph.face);
+    if (c.depth) __stcs(c.depth + pix, depth);
+    if (c.rgba) __stcs(c.rgba + pix, hit ? shade(ph.word, ph.face, visible, p.sun_n) : kSky);
+}
+
+// One pixel: its primary ray, then (with shadows) the shadow ray, which
+// reuses the same traversal loop and registers.
 template <bool SHADOWS, bool STATS>
 __device__ __forceinline__ void trace_pixel(const RenderParams &p, const CamDev &c, int32_t px,
                                             int32_t py, Counters &cnt, Counters &scnt,
@@ -342,8 +362,7 @@ __device__ __forceinline__ void trace_pixel(const RenderParams &p, const CamDev 
     r.dx = c.F[0] + a * c.R[0] + b * c.U[0];
     r.dy = c.F[1] + a * c.R[1] + b * c.U[1];
     r.dz = c.F[2] + a * c.R[2] + b * c.U[2];
-    // primary hit, kept while the shadow ray reuses the traversal loop
-    Hit ph;
+    Hit ph;  // primary hit, kept while the shadow ray runs
     float depth = __int_as_float(0x7f800000);
     bool visible = true;
     bool shadow_pass = false;
@@ -352,7 +371,7 @@ __device__ __forceinline__ void trace_pixel(const RenderParams &p, const CamDev 
         if (!SHADOWS || !shadow_pass) {
             trace_ray<STATS>(p.world, r, p.mip_start, p.max_steps, h, cnt);
         } else {
-            trace_ray<STATS>(p.world, r, p.mip_start, p.max_steps, h, scnt);
+            trace_ray<STATS>(p.world, r, p.shadow_mip, p.max_steps, h, scnt);
         }
         if (h.face == kFaceError) err = true;
         if (SHADOWS && shadow_pass) {
@@ -393,18 +412,10 @@ __device__ __forceinline__ void trace_pixel(const RenderParams &p, const CamDev 
         if (STATS) nshadow++;
         shadow_pass = true;
     }
-    const uint32_t pix = (uint32_t)py * c.w + (uint32_t)px;
-    const bool hit = ph.face < kFaceError;
-    if (SHADOWS && c.shadow) __stcs(c.shadow + pix, (uint8_t)(visible ? 0 : 1));
-    if (c.hit_cell)
-        __stcs(c.hit_cell + pix,
-               hit ? (uint32_t)ph.cy * (uint32_t)p.world.W + (uint32_t)ph.cx : 0xFFFFFFFFu);
-    if (c.layer) __stcs(c.layer + pix, hit ? ph.layer : (uint8_t)255);
-    if (c.face) __stcs(c.face + pix, ph.face);
-    if (c.depth) __stcs(c.depth + pix, depth);
-    if (c.rgba) __stcs(c.rgba + pix, hit ? shade(ph.word, ph.face, visible, p.sun_n) : kSky);
+    store_pixel(p, c, (uint32_t)py * c.w + (uint32_t)px, ph, depth, visible, SHADOWS);
 }
 
+// One warp renders one tile: lane l traces the tile's pixels l, l+32, ...
 template <bool SHADOWS, bool STATS>
 __device__ __forceinline__ void trace_tile(const RenderParams &p, const CamDev &c,
                                            uint32_t local_tile, int lane) {
@@ -688,6 +699,9 @@ extern "C" int hf_render_noalloc(hf_ctx *ctx, const hf_camera *cams, uint32_t n,
     p.tile_w_log2 = twl;
     p.tile_h_log2 = thl;
     p.mip_start = (int32_t)(mip > (uint32_t)v.world.L ? (uint32_t)v.world.L : mip);
+    p.shadow_mip = (int32_t)((uint32_t)p.mip_start + kShadowMipExtra > (uint32_t)v.world.L
+                                 ? (uint32_t)v.world.L
+                                 : (uint32_t)p.mip_start + kShadowMipExtra);
     p.max_steps = (int32_t)steps;
     const double sn = sqrt((double)sun[0] * sun[0] + (double)sun[1] * sun[1] +
                            (double)sun[2] * sun[2]);
