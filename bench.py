@@ -48,6 +48,42 @@ def _dist():
     return ws, rank, local
 
 
+# ------------------------------------------------------------- ncu traffic
+
+TRACE_SOURCES = ("paper_2608_17390_gb300/csrc/hf_trace.cu", "paper_2608_17390_gb300/csrc/hf_internal.h")
+
+
+def trace_source_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    for rel in TRACE_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic(workload, rays, scale):
+    """DRAM bytes (read + write) per launch of the trace kernel, from the
+    committed ncu summary of this workload: its measured bytes per ray times
+    the rays of one launch here.  None when there is no summary, or when the
+    kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "trace_batched_%s.md" % workload)
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    if fields.get("kernel_source_sha256") != trace_source_hash():
+        return None
+    try:
+        return float(fields["dram_bytes_per_ray"]) * rays
+    except (KeyError, ValueError):
+        return None
+
+
 # ------------------------------------------------------------------ workloads
 
 def workload(name, rank=0, scale=1):
@@ -323,13 +359,7 @@ def run_hf(args):
     alg_bytes = fetch_b + out_b
     r_ms = float(np.mean(render_ms))
     achieved = alg_bytes / (r_ms / 1e3) / 1e9
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "traffic_%s.json" % args.workload)
-    if os.path.exists(tfile):
-        try:
-            traffic = json.load(open(tfile)).get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = _profiled_traffic(args.workload, rays, args.scale)
     line = {
         "metric": "primary rays/s (batched, exact two-interval height-field ray cast)",
         "value": value, "unit": "primary rays/s", "n_gpus": ws, "steps": args.steps,

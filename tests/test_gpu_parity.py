@@ -418,3 +418,30 @@ def test_flat_fetch_counter_matches_oracle_steps(hf, c1):
         assert st["cell_fetches"] == int(o["steps"].sum())
     finally:
         hf.hf_destroy(ctx)
+
+
+def test_nowait_admission_reports_busy(hf):
+    """Admission without waiting: when every render slot is in flight,
+    HF_NOWAIT returns HF_E_BUSY instead of blocking; nothing is lost."""
+    cfg = synth.config_c3(scale=2)
+    cells, cams = cfg["cells"], cfg["cams"]
+    ctx = _ctx(hf, cells)
+    try:
+        info = hf.hf_info(ctx)
+        outs = hf.alloc_outputs(cams)
+        busy = 0
+        for _ in range(info["render_slots"] + 4):
+            try:
+                hf.hf_render(ctx, cams, outs, hf.make_opts(flags=hf.HF_NOWAIT))
+            except hf.HFError as e:
+                assert e.code == hf.HF_E_BUSY
+                busy += 1
+        hf.hf_sync(ctx)
+        assert busy >= 1
+        g = gpu_render(hf, ctx, cams[:2])
+        for i in range(2):
+            pix = sample_pixels(int(cams[i]["w"]), int(cams[i]["h"]), 300, i)
+            o = oracle.render(cells, cams[i], pix=pix, nthreads=NT)
+            compare({k: v[pix] for k, v in g[i].items()}, o, what="after busy cam %d" % i)
+    finally:
+        hf.hf_destroy(ctx)
