@@ -251,6 +251,24 @@ def run_hf(args):
         cells[y0:y0 + blk.shape[0], x0:x0 + blk.shape[1]] = blk
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def _ev_ms(fn, reps=5):
+        ts = []
+        for _ in range(reps):
+            with torch.cuda.stream(stream):
+                flush.fill_(3)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            hf.hf_sync(ctx)
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    # rows a2 / a3: full pyramid build, and one crater edit (H2D of the rect +
+    # incremental repair), each on the context stream, L2 flushed before
+    build_ms = _ev_ms(lambda: hf.hf_rebuild(ctx))
+    edit_ms = _ev_ms(do_edit)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
 
@@ -375,6 +393,8 @@ def run_hf(args):
         "plain_rays_per_s": plain,
         "batched_over_plain": (value / ws / plain) if plain else None,
         "render_ms": r_ms,
+        "pyramid_build_ms": build_ms,
+        "edit_repair_ms": edit_ms,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic,
                      "peak_source": src,
