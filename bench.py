@@ -86,7 +86,7 @@ def _profiled_traffic(workload, rays, scale):
 
 # ------------------------------------------------------------------ workloads
 
-def workload(name, rank=0, scale=1):
+def workload(name, rank=0, scale=1, frames_per_step=100):
     import synth
 
     if name == "c3":
@@ -106,10 +106,10 @@ def workload(name, rank=0, scale=1):
                     cams=cfg["cams"], shadows=False, edit=False)
     if name == "c4":
         cells = synth.config_c4()["cells"]
-        return dict(name="C4 large world: 2048x16384 grid (seed 4, 30% slabs), 1000-frame "
-                         "1920x1080 fly-through; one step = 100 frames in one batch",
+        return dict(name="C4 large world: 2048x16384 grid (seed 4, 30%% slabs), 1000-frame "
+                         "1920x1080 fly-through; one step = %d frames in one batch" % frames_per_step,
                     cells=cells, cams=synth.config_c4_frames(cells, 1000), shadows=False,
-                    edit=False, frames_per_step=100)
+                    edit=False, frames_per_step=frames_per_step)
     raise SystemExit("unknown workload " + name)
 
 
@@ -212,7 +212,7 @@ def run_hf(args):
     import paper_2608_17390_gb300 as hf
     import synth
 
-    wl = workload(args.workload, rank, args.scale)
+    wl = workload(args.workload, rank, args.scale, args.frames_per_step)
     if args.scale != 1:
         wl["name"] += " (resolutions divided by %d)" % args.scale
     cells = wl["cells"].copy()
@@ -512,6 +512,8 @@ def main():
     ap.add_argument("--impl", default="hf", choices=["hf", "reference"])
     ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4", "c5"])
     ap.add_argument("--serve-requests", type=int, default=2200)
+    ap.add_argument("--frames-per-step", type=int, default=100,
+                    help="large-world fly-through frames rendered per step (one batch)")
     ap.add_argument("--mip", type=int, default=0xFFFFFFFF)
     ap.add_argument("--tile-w", type=int, default=0)
     ap.add_argument("--tile-h", type=int, default=0)

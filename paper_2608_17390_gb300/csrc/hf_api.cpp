@@ -286,8 +286,7 @@ static int create_impl(const hf_desc *d, hf_ctx *c) {
     const size_t stride = d->row_stride ? d->row_stride : d->width;
     CK(cudaMemcpy2DAsync(c->d_world, (size_t)c->W * 4, d->cells, stride * 4, (size_t)c->W * 4,
                          c->H, cudaMemcpyHostToDevice, c->stream));
-    if (hf::pyramid_repair(c->d_world, c->wd, 0, 0, (int32_t)c->W, (int32_t)c->H, c->stream))
-        return HF_E_CUDA;
+    if (hf::pyramid_build(c->d_world, c->wd, c->stream)) return HF_E_CUDA;
     if (cudaMalloc(&c->d_status, sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc(&c->d_stats, 5 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaHostAlloc(&c->h_status, sizeof(uint32_t), cudaHostAllocDefault) != cudaSuccess) {
@@ -392,8 +391,7 @@ int hf_rebuild(hf_ctx *c) {
     CK(cudaSetDevice(c->device));
     for (auto &s : c->slots)
         if (s.pending) CK(cudaStreamWaitEvent(c->stream, s.done, 0));
-    if (hf::pyramid_repair(c->d_world, c->wd, 0, 0, (int32_t)c->W, (int32_t)c->H, c->stream))
-        return HF_E_CUDA;
+    if (hf::pyramid_build(c->d_world, c->wd, c->stream)) return HF_E_CUDA;
     CK(cudaEventRecord(c->edit_done, c->stream));
     return HF_OK;
 }

@@ -93,5 +93,11 @@ int ctx_view(const ::hf_ctx *ctx, CtxView *out);
 // [x0, x1) x [y0, y1) at every level 1..L, in order.
 int pyramid_repair(uint32_t *world, const WorldDev &w, int32_t x0, int32_t y0, int32_t x1,
                    int32_t y1, void *stream);
+// Same, for levels k_from..L only (levels below k_from must already be current).
+int pyramid_repair_from(uint32_t *world, const WorldDev &w, int k_from, int32_t x0, int32_t y0,
+                        int32_t x1, int32_t y1, void *stream);
+// Full build of levels 1..L from the cells: levels 1..6 by 64 x 64 tiles in
+// shared memory (cells read once), the rest by repair of the whole grid.
+int pyramid_build(uint32_t *world, const WorldDev &w, void *stream);
 
 }  // namespace hf

@@ -6,8 +6,11 @@
 // the per-byte max/min of its (up to four) children, so after an edit of a cell
 // rectangle only the nodes over that rectangle change, level by level: the
 // "rebuild affected cells and their ancestors" of the paper's Sections 2 and
-// 3.2, applied to a 2.5-D min/max hierarchy.  A full build is the repair of
-// the whole grid, so build and repair run the same kernels.
+// 3.2, applied to a 2.5-D min/max hierarchy.  The full build (hf_create,
+// hf_rebuild) makes levels 1..6 per 64 x 64 tile in shared memory so the cells
+// are read from HBM once; repair recomputes the nodes over a rectangle level by
+// level.  The two paths share only the byte-wise combine, and the tests compare
+// each with the oracle's pyramid.
 #include <cuda_runtime.h>
 
 #include "hf_internal.h"
@@ -25,9 +28,10 @@ __device__ __forceinline__ uint32_t cell_node(uint32_t c) {
     return h0 | ((slab ? h1 : 255u) << 8) | ((slab ? h2 : h0) << 16);
 }
 
-// byte0 and byte2 by max, byte1 by min
+// byte0 and byte2 by max, byte1 by min (each field compared in place)
 __device__ __forceinline__ uint32_t combine(uint32_t a, uint32_t b) {
-    return (__vmaxu4(a, b) & 0x00FF00FFu) | (__vminu4(a, b) & 0x0000FF00u);
+    return max(a & 0x0000FFu, b & 0x0000FFu) | min(a & 0x00FF00u, b & 0x00FF00u) |
+           max(a & 0xFF0000u, b & 0xFF0000u);
 }
 
 __device__ __forceinline__ uint32_t reduce_children(const uint32_t *src, uint32_t stride,
@@ -80,13 +84,119 @@ __global__ void __launch_bounds__(kTailThreads) k_pyr_tail(uint32_t *world, cons
     }
 }
 
+// Full build, levels 1..min(6, L) of one 64 x 64 cell tile per block: the
+// cells are read from HBM once (coalesced), every level of the tile is made in
+// shared memory from the one below, and each level is written once.
+constexpr int kTile = 64;
+constexpr int kTileLevels = 6;  // 64 -> 1
+constexpr int kBuildThreads = 256;
+
+__global__ void __launch_bounds__(kBuildThreads) k_pyr_build_tiles(uint32_t *world,
+                                                                   const WorldDev w,
+                                                                   int32_t top) {
+    // level-2 nodes of the tile (16 x 16), then levels 3..6 back to back
+    __shared__ uint32_t s_lv[16 * 16 + 8 * 8 + 4 * 4 + 2 * 2 + 1];
+    const int32_t bx = blockIdx.x * kTile, by = blockIdx.y * kTile;
+    // this thread's 4 x 4 cell block inside the tile
+    const int qx = threadIdx.x & 15, qy = threadIdx.x >> 4;
+    const int32_t cx0 = bx + 4 * qx, cy0 = by + 4 * qy;
+    const uint32_t *cells = world;  // level 0
+    uint32_t c[4][4];
+    if (cx0 + 4 <= w.W && cy0 + 4 <= w.H && (w.W & 3) == 0) {
+        uint4 v[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)  // four 16-byte loads issued before use
+            v[r] = __ldg(reinterpret_cast<const uint4 *>(cells + (uint32_t)(cy0 + r) * (uint32_t)w.W +
+                                                         (uint32_t)cx0));
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            c[r][0] = cell_node(v[r].x);
+            c[r][1] = cell_node(v[r].y);
+            c[r][2] = cell_node(v[r].z);
+            c[r][3] = cell_node(v[r].w);
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int32_t x = cx0 + q, y = cy0 + r;
+                c[r][q] = (x < w.W && y < w.H)
+                              ? cell_node(__ldg(cells + (uint32_t)y * (uint32_t)w.W + (uint32_t)x))
+                              : kIdentity;
+            }
+    }
+    // levels 1 and 2 of the block in registers
+    uint32_t l1[2][2];
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+            l1[b][a] = combine(combine(c[2 * b][2 * a], c[2 * b][2 * a + 1]),
+                               combine(c[2 * b + 1][2 * a], c[2 * b + 1][2 * a + 1]));
+    const uint32_t l2 = combine(combine(l1[0][0], l1[0][1]), combine(l1[1][0], l1[1][1]));
+    {
+        const int32_t gx = cx0 >> 1, gy = cy0 >> 1;
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+                if ((uint32_t)(gx + a) < w.stride[1] && (uint32_t)(gy + b) < w.rows[1])
+                    world[w.off[1] + (uint32_t)(gy + b) * w.stride[1] + (uint32_t)(gx + a)] =
+                        l1[b][a];
+    }
+    if (top >= 2) {
+        const int32_t gx = cx0 >> 2, gy = cy0 >> 2;
+        if ((uint32_t)gx < w.stride[2] && (uint32_t)gy < w.rows[2])
+            world[w.off[2] + (uint32_t)gy * w.stride[2] + (uint32_t)gx] = l2;
+    }
+    s_lv[threadIdx.x] = l2;
+    __syncthreads();
+    // levels 3..top from the 16 x 16 level-2 nodes in shared memory
+    int n = 16, src = 0, dst = 256;
+    for (int k = 3; k <= top; ++k) {
+        const int m = n >> 1;
+        const int32_t ox = bx >> k, oy = by >> k;  // tile origin at level k
+        if (threadIdx.x < m * m) {
+            const int a = threadIdx.x % m, b = threadIdx.x / m;
+            const uint32_t *p0 = s_lv + src + (2 * b) * n + 2 * a;
+            const uint32_t v = combine(combine(p0[0], p0[1]), combine(p0[n], p0[n + 1]));
+            s_lv[dst + threadIdx.x] = v;
+            const int32_t gx = ox + a, gy = oy + b;
+            if ((uint32_t)gx < w.stride[k] && (uint32_t)gy < w.rows[k])
+                world[w.off[k] + (uint32_t)gy * w.stride[k] + (uint32_t)gx] = v;
+        }
+        __syncthreads();
+        src = dst;
+        dst += m * m;
+        n = m;
+    }
+}
+
 }  // namespace
+
+int pyramid_build(uint32_t *world, const WorldDev &w, void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (w.L == 0) return 0;
+    const int top = w.L < kTileLevels ? w.L : kTileLevels;
+    const dim3 grid((w.W + kTile - 1) / kTile, (w.H + kTile - 1) / kTile);
+    k_pyr_build_tiles<<<grid, kBuildThreads, 0, s>>>(world, w, top);
+    if (cudaGetLastError() != cudaSuccess) return -1;
+    if (top == w.L) return 0;
+    // levels top+1 .. L from level `top`, over the whole grid (small)
+    return pyramid_repair_from(world, w, top + 1, 0, 0, w.W, w.H, stream);
+}
 
 int pyramid_repair(uint32_t *world, const WorldDev &w, int32_t x0, int32_t y0, int32_t x1,
                    int32_t y1, void *stream) {
+    return pyramid_repair_from(world, w, 1, x0, y0, x1, y1, stream);
+}
+
+int pyramid_repair_from(uint32_t *world, const WorldDev &w, int k_from, int32_t x0, int32_t y0,
+                        int32_t x1, int32_t y1, void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
-    if (x1 <= x0 || y1 <= y0 || w.L == 0) return 0;
-    int k = 1;
+    if (x1 <= x0 || y1 <= y0 || w.L == 0 || k_from > w.L) return 0;
+    int k = k_from;
     for (; k <= w.L; ++k) {
         const int32_t i0 = x0 >> k, i1 = (x1 - 1) >> k, j0 = y0 >> k, j1 = (y1 - 1) >> k;
         const int64_t ni = i1 - i0 + 1, nj = j1 - j0 + 1;

@@ -1,0 +1,48 @@
+"""bench.py on the CPU: every workload builds, the reference arm's JSON line
+has the contract's keys, and the traffic lookup follows the profile summary."""
+
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+@pytest.mark.parametrize("name", ["c1", "c2", "c3", "c4"])
+def test_workloads_build(name):
+    import bench
+
+    wl = bench.workload(name, frames_per_step=7)
+    assert wl["cells"].ndim == 2 and len(wl["cams"]) >= 1 and wl["name"]
+    if name == "c4":
+        assert "7 frames" in wl["name"] and len(wl["cams"]) == 1000
+
+
+def test_reference_arm_line():
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "c1",
+                        "--steps", "1", "--warmup", "0"], cwd=ROOT, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "higher_is_better",
+              "cpu_baseline", "e2e", "config"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+
+
+def test_traffic_lookup_tracks_the_kernel_source():
+    import bench
+
+    t = bench._profiled_traffic("c3", 1000, 1)
+    path = os.path.join(ROOT, "profiles", "trace_batched_c3.md")
+    text = open(path).read()
+    if bench.trace_source_hash() in text:
+        assert t is not None and t > 0
+    else:
+        assert t is None
+    assert bench._profiled_traffic("no_such_workload", 1000, 1) is None
