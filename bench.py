@@ -479,6 +479,78 @@ def run_serve(args):
     print(json.dumps(line))
 
 
+def run_protocol(args):
+    """The paper's protocol shape (its Sections 4.3 and 5.2): 12 viewpoints at
+    pitch 0 / -30 / -60 / -90, 1280x800, far 600, on the large world.  Times
+    the exact cast and the paper's fixed-step march (steady-state frames and
+    one batched launch of all 12 views) and scores the march against the exact
+    cast with the Section 4.2 metrics."""
+    import torch
+
+    import __graft_entry__
+
+    torch.cuda.set_device(0)
+    __graft_entry__.build_library()
+    import paper_2608_17390_gb300 as hf
+    from paper_2608_17390_gb300 import metrics
+    import synth
+
+    cells = synth.config_c4()["cells"]
+    cams = synth.protocol_cameras(cells)
+    stream = torch.cuda.Stream()
+    ctx = hf.hf_create(cells, stream=stream.cuda_stream)
+    fields = ("hit_cell", "layer", "depth")
+    outs = hf.alloc_outputs(cams, fields=fields)
+
+    def ev_ms(fn, reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for r in range(reps):
+            fn(r)
+        b.record(stream)
+        hf.hf_sync(ctx)
+        return a.elapsed_time(b) / reps
+
+    exact = hf.make_opts(stream=stream.cuda_stream)
+    frame = lambda r: hf.hf_render(ctx, cams[r % 12:r % 12 + 1], outs[r % 12:r % 12 + 1], exact)
+    batch = lambda r: hf.hf_render(ctx, cams, outs, exact)
+    ev_ms(frame, 24)
+    res = {"exact": {"frame_ms": ev_ms(frame, 40), "batch12_ms": ev_ms(batch, 10)}}
+    ref = [{k: v.cpu().numpy() for k, v in o.items()} for o in outs]
+    for st in (16, 64, 128, 256):
+        mo = hf.make_march_opts(steps=st, far_dist=600.0, stream=stream.cuda_stream)
+        mframe = lambda r: hf.hf_render_march(ctx, cams[r % 12:r % 12 + 1],
+                                              outs[r % 12:r % 12 + 1], mo)
+        mbatch = lambda r: hf.hf_render_march(ctx, cams, outs, mo)
+        ev_ms(mframe, 24)
+        row = {"frame_ms": ev_ms(mframe, 40), "batch12_ms": ev_ms(mbatch, 10)}
+        got = [{k: v.cpu().numpy() for k, v in o.items()} for o in outs]
+        per_pitch = {}
+        for p_i, pitch in enumerate(synth.PROTOCOL_PITCHES):
+            ms = []
+            for v in range(3):
+                i = 3 * p_i + v
+                h, w = int(cams[i]["h"]), int(cams[i]["w"])
+                rd = ref[i]["depth"].reshape(h, w).astype(np.float64)
+                rh = np.isfinite(rd) & (rd <= 600.0)  # the exact cast, clipped at the same far distance
+                gd = got[i]["depth"].reshape(h, w).astype(np.float64)
+                ms.append(metrics.compare(rh, rd, np.isfinite(gd), gd))
+            per_pitch["%d" % int(pitch)] = {k: float(np.mean([m[k] for m in ms])) for k in ms[0]}
+        row["metrics_by_pitch"] = per_pitch
+        res["march_%d" % st] = row
+    hf.hf_destroy(ctx)
+    line = {"metric": "frame time, paper protocol (12 views, 1280x800): exact cast vs the "
+                      "paper's fixed-step march, with Section 4.2 metrics of the march",
+            "value": res["exact"]["frame_ms"], "unit": "ms per 1280x800 frame (exact cast)",
+            "n_gpus": 1, "steps": 40, "warmup": 24, "higher_is_better": False,
+            "vs_baseline": None, "dtype": "i32 (exact) / f32 (march)", "data": "synthetic",
+            "config": {"workload": "2048x16384 grid (seed 4, 30% slabs), 3 views at each pitch "
+                                   "0/-30/-60/-90, 1280x800, hfov 75, far 600 (march); "
+                                   "steady-state frames, primary rays only"},
+            "results": res}
+    print(json.dumps(line))
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -510,7 +582,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hf", choices=["hf", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--workload", default="c3",
+                    choices=["c1", "c2", "c3", "c4", "c5", "protocol"])
     ap.add_argument("--serve-requests", type=int, default=2200)
     ap.add_argument("--frames-per-step", type=int, default=100,
                     help="large-world fly-through frames rendered per step (one batch)")
@@ -531,6 +604,8 @@ def main():
         run_reference(args)
     elif args.workload == "c5":
         run_serve(args)
+    elif args.workload == "protocol":
+        run_protocol(args)
     else:
         run_hf(args)
 

@@ -193,6 +193,30 @@ int hf_render(hf_ctx *ctx, const hf_camera *cams, uint32_t n, const hf_outputs *
 int hf_render_noalloc(hf_ctx *ctx, const hf_camera *cams, uint32_t n, const hf_outputs *outs,
                       const hf_render_opts *opts);
 
+/* Options of the fixed-step comparison marcher. */
+typedef struct {
+    uint32_t steps;          /* forward samples over the clipped segment; 0 = 128 */
+    uint32_t bisections;     /* bisection iterations after the first solid sample; 0 = 4 */
+    float far_dist;          /* far plane distance in world units; 0 = 600 */
+    uint32_t tile_w, tile_h; /* warp tile as in hf_render_opts; 0,0 = 8 x 4 */
+    uint32_t flags;          /* HF_SYNC */
+    void *cuda_stream;       /* NULL = the context's stream */
+} hf_march_opts;
+
+/* The paper's own height-field ray march (Section 3.1), for comparison with
+ * the exact cast: per pixel ray, clip the segment at the far distance and, for
+ * a descending ray, at z = 0; take `steps` samples spaced uniformly over it
+ * (the paper's text; its listing's loop would space them geometrically); stop
+ * at the first sample inside a solid interval of the cell holding it; refine
+ * with `bisections` halvings.  float32 arithmetic in a fixed order, no fused
+ * multiply-add.  It can step over features thinner than its sample spacing.
+ * Writes hit_cell, layer and depth (face, rgba, shadow are not written); a ray
+ * with no solid sample misses (0xFFFFFFFF, 255, +inf).  Same ordering rules as
+ * hf_render.  Errors: as hf_render (steps or bisections above 65536, or a
+ * non-positive far distance, are HF_E_INVALID_ARG). */
+int hf_render_march(hf_ctx *ctx, const hf_camera *cams, uint32_t n, const hf_outputs *outs,
+                    const hf_march_opts *opts);
+
 /* Wait for all work the context issued (every render slot and the context
  * stream).  Returns HF_E_STEP_LIMIT if any ray of any render since the last
  * hf_sync hit its step guard (and clears that flag), else HF_OK / HF_E_CUDA. */

@@ -1,7 +1,8 @@
 """Python binding of libhf.so: exact two-interval height-field ray casting on GB300.
 
 A thin ctypes layer over the C ABI in include/hf.h, with the same names:
-``hf_create``, ``hf_edit``, ``hf_render``, ``hf_render_noalloc``, ``hf_sync``, ``hf_destroy``,
+``hf_create``, ``hf_edit``, ``hf_render``, ``hf_render_noalloc``, ``hf_render_march``,
+``hf_sync``, ``hf_destroy``,
 ``hf_camera_from_pose``, ``hf_validate_camera``, ``hf_validate_cells``,
 ``hf_strerror``, ``hf_info``, ``hf_read_cells``, ``hf_read_pyramid``,
 ``hf_rebuild``, ``hf_stats``.  It only marshals arguments: every step of the
@@ -76,6 +77,13 @@ class hf_render_opts(ctypes.Structure):
                 ("cuda_stream", ctypes.c_void_p)]
 
 
+class hf_march_opts(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_uint32), ("bisections", ctypes.c_uint32),
+                ("far_dist", ctypes.c_float), ("tile_w", ctypes.c_uint32),
+                ("tile_h", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
 class hf_info_t(ctypes.Structure):
     _fields_ = [("width", ctypes.c_uint32), ("height", ctypes.c_uint32),
                 ("levels", ctypes.c_uint32), ("render_slots", ctypes.c_uint32),
@@ -99,6 +107,7 @@ _SIGS = {
     "hf_edit": ([_P, _U32, _U32, _U32, _U32, _P, ctypes.c_size_t], ctypes.c_int),
     "hf_render": ([_P, _P, _U32, _P, ctypes.POINTER(hf_render_opts)], ctypes.c_int),
     "hf_render_noalloc": ([_P, _P, _U32, _P, ctypes.POINTER(hf_render_opts)], ctypes.c_int),
+    "hf_render_march": ([_P, _P, _U32, _P, ctypes.POINTER(hf_march_opts)], ctypes.c_int),
     "hf_sync": ([_P], ctypes.c_int),
     "hf_destroy": ([_P], ctypes.c_int),
     "hf_camera_from_pose": ([ctypes.c_double] * 6 + [_U32, _U32, ctypes.POINTER(hf_camera)],
@@ -228,6 +237,24 @@ def hf_render_noalloc(ctx, cams, outs, opts=None):
     popts = ctypes.byref(opts) if opts is not None else None
     _check(lib.hf_render_noalloc(ctx, recs.ctypes.data if n else None, n, oarr, popts),
            "hf_render_noalloc")
+
+
+def make_march_opts(steps=0, bisections=0, far_dist=0.0, tile_w=0, tile_h=0, flags=0,
+                    stream=None):
+    return hf_march_opts(steps, bisections, far_dist, tile_w, tile_h, flags, stream)
+
+
+def hf_render_march(ctx, cams, outs, opts=None):
+    """The paper's fixed-step ray march (comparison method; see include/hf.h).
+    Writes hit_cell, layer and depth of each output dict."""
+    recs = camera_records(cams)
+    n = len(recs)
+    if len(outs) != n:
+        raise ValueError("one output set per camera")
+    oarr = _outputs_array(outs)
+    popts = ctypes.byref(opts) if opts is not None else None
+    _check(lib.hf_render_march(ctx, recs.ctypes.data if n else None, n, oarr, popts),
+           "hf_render_march")
 
 
 def hf_sync(ctx):

@@ -65,6 +65,7 @@ struct hf_ctx {
     uint32_t *h_status = nullptr;
     unsigned long long *d_stats = nullptr;
     int occ[2][2] = {{0, 0}, {0, 0}};
+    int occ_march = 0;
 };
 
 #define CK(call)                                   \
@@ -303,6 +304,7 @@ static int create_impl(const hf_desc *d, hf_ctx *c) {
         for (int st = 0; st < 2; ++st)
             if (hf::trace_batched_occupancy(sh, st, &c->occ[sh][st]) || c->occ[sh][st] < 1)
                 return HF_E_CUDA;
+    if (hf::march_occupancy(&c->occ_march) || c->occ_march < 1) return HF_E_CUDA;
     CK(cudaStreamSynchronize(c->stream));
     return HF_OK;
 }
@@ -528,23 +530,20 @@ static int launch_graph(hf_ctx *c, Slot &s, const GraphKey &key, const hf::Rende
     return HF_OK;
 }
 
-int hf_render(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_outputs *outs,
-              const hf_render_opts *opts) {
-    if (!c) return HF_E_INVALID_ARG;
-    if (n == 0) return HF_OK;
-    if (!cams || !outs || n > HF_MAX_CAMERAS) return HF_E_INVALID_ARG;
-    hf_render_opts o{};
-    if (opts) o = *opts;
-    else o.mip_start = HF_MIP_AUTO;
-    const uint32_t tw = o.tile_w ? o.tile_w : 8, th = o.tile_h ? o.tile_h : 4;
+// Validates the cameras, takes a render slot and fills its camera table.
+struct Batch {
+    int slot;
+    size_t bytes, bucket;
+    std::vector<uint32_t> tiles;
+    hf::RenderParams p;
+    cudaStream_t stream;
+};
+
+static int prepare_batch(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_outputs *outs,
+                         uint32_t tw, uint32_t th, bool nowait, void *user_stream, Batch &b) {
     const int twl = ilog2_exact(tw), thl = ilog2_exact(th);
     if (twl < 0 || thl < 0 || tw * th < 32 || tw * th > 256 || tw > 256 || th > 256)
         return HF_E_INVALID_ARG;
-    int32_t sun[3] = {o.sun[0], o.sun[1], o.sun[2]};
-    if (sun[0] == 0 && sun[1] == 0 && sun[2] == 0)
-        for (int i = 0; i < 3; ++i) sun[i] = kDefaultSun[i];
-    for (int i = 0; i < 3; ++i)
-        if (iabs64(sun[i]) >= kLimit21) return HF_E_INVALID_ARG;
     uint64_t total_tiles = 0;
     for (uint32_t i = 0; i < n; ++i) {
         if (hf_validate_camera(c->W, c->H, &cams[i]) != HF_OK) return HF_E_INVALID_ARG;
@@ -552,31 +551,21 @@ int hf_render(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_outputs *ou
         total_tiles += tx * ty;
     }
     if (total_tiles >= 0xFFFFFFFFull) return HF_E_INVALID_ARG;
-    const bool shadows = (o.flags & HF_SHADOWS) != 0;
-    const bool stats = (o.flags & HF_STATS) != 0;
-    const uint32_t mip = o.mip_start == HF_MIP_AUTO ? hf::kDefaultMipStart : o.mip_start;
-    const uint32_t mip_c = mip > c->L ? c->L : mip;
-    const uint64_t guard = 4ull * (c->W + c->H) + 64;
-    const uint32_t steps = o.max_steps ? o.max_steps : (uint32_t)(guard > 0x7FFFFFFF ? 0x7FFFFFFF : guard);
-    if (steps > 0x7FFFFFFFu) return HF_E_INVALID_ARG;
-
     CK(cudaSetDevice(c->device));
-    cudaStream_t stream = o.cuda_stream ? (cudaStream_t)o.cuda_stream : c->stream;
-    int si = 0;
-    int rc = acquire_slot(c, (o.flags & HF_NOWAIT) != 0, &si);
+    b.stream = user_stream ? (cudaStream_t)user_stream : c->stream;
+    int rc = acquire_slot(c, nowait, &b.slot);
     if (rc != HF_OK) return rc;
-    Slot &s = c->slots[si];
-    const size_t bytes = sizeof(hf::BatchHeader) + (size_t)n * sizeof(hf::CamDev);
-    const size_t bucket = (bytes + kScratchAlign - 1) & ~(kScratchAlign - 1);
-    rc = ensure_slot_cap(s, bucket);
+    Slot &s = c->slots[b.slot];
+    b.bytes = sizeof(hf::BatchHeader) + (size_t)n * sizeof(hf::CamDev);
+    b.bucket = (b.bytes + kScratchAlign - 1) & ~(kScratchAlign - 1);
+    rc = ensure_slot_cap(s, b.bucket);
     if (rc != HF_OK) return rc;
-
     auto *hdr = (hf::BatchHeader *)s.h_staging;
     std::memset(hdr, 0, sizeof(*hdr));
     hdr->n_cams = n;
     hdr->total_tiles = (uint32_t)total_tiles;
     auto *cd = (hf::CamDev *)((char *)s.h_staging + sizeof(hf::BatchHeader));
-    std::vector<uint32_t> tiles(n);
+    b.tiles.assign(n, 0);
     uint32_t base = 0;
     for (uint32_t i = 0; i < n; ++i) {
         const hf_camera &k = cams[i];
@@ -590,9 +579,9 @@ int hf_render(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_outputs *ou
         v.w = k.w;
         v.h = k.h;
         v.tiles_x = (k.w + tw - 1) / tw;
-        tiles[i] = v.tiles_x * ((k.h + th - 1) / th);
+        b.tiles[i] = v.tiles_x * ((k.h + th - 1) / th);
         v.tile_base = base;
-        base += tiles[i];
+        base += b.tiles[i];
         v.hit_cell = outs[i].hit_cell;
         v.layer = outs[i].layer;
         v.face = outs[i].face;
@@ -600,15 +589,56 @@ int hf_render(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_outputs *ou
         v.rgba = outs[i].rgba;
         v.shadow = outs[i].shadow;
     }
+    std::memset(&b.p, 0, sizeof(b.p));
+    b.p.world = c->wd;
+    b.p.hdr = (hf::BatchHeader *)s.d_scratch;
+    b.p.cams = (const hf::CamDev *)((char *)s.d_scratch + sizeof(hf::BatchHeader));
+    b.p.status = c->d_status;
+    b.p.stats = c->d_stats;
+    b.p.tile_w_log2 = twl;
+    b.p.tile_h_log2 = thl;
+    if (b.stream != c->stream) CK(cudaStreamWaitEvent(b.stream, c->edit_done, 0));
+    return HF_OK;
+}
 
-    hf::RenderParams p{};
-    p.world = c->wd;
-    p.hdr = (hf::BatchHeader *)s.d_scratch;
-    p.cams = (const hf::CamDev *)((char *)s.d_scratch + sizeof(hf::BatchHeader));
-    p.status = c->d_status;
-    p.stats = c->d_stats;
-    p.tile_w_log2 = twl;
-    p.tile_h_log2 = thl;
+static int finish_batch(hf_ctx *c, Batch &b, bool sync) {
+    Slot &s = c->slots[b.slot];
+    CK(cudaEventRecord(s.done, b.stream));
+    s.pending = true;
+    if (sync) {
+        CK(cudaEventSynchronize(s.done));
+        s.pending = false;
+        return read_status(c);
+    }
+    return HF_OK;
+}
+
+int hf_render(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_outputs *outs,
+              const hf_render_opts *opts) {
+    if (!c) return HF_E_INVALID_ARG;
+    if (n == 0) return HF_OK;
+    if (!cams || !outs || n > HF_MAX_CAMERAS) return HF_E_INVALID_ARG;
+    hf_render_opts o{};
+    if (opts) o = *opts;
+    else o.mip_start = HF_MIP_AUTO;
+    const uint32_t tw = o.tile_w ? o.tile_w : 8, th = o.tile_h ? o.tile_h : 4;
+    int32_t sun[3] = {o.sun[0], o.sun[1], o.sun[2]};
+    if (sun[0] == 0 && sun[1] == 0 && sun[2] == 0)
+        for (int i = 0; i < 3; ++i) sun[i] = kDefaultSun[i];
+    for (int i = 0; i < 3; ++i)
+        if (iabs64(sun[i]) >= kLimit21) return HF_E_INVALID_ARG;
+    const bool shadows = (o.flags & HF_SHADOWS) != 0;
+    const bool stats = (o.flags & HF_STATS) != 0;
+    const uint32_t mip = o.mip_start == HF_MIP_AUTO ? hf::kDefaultMipStart : o.mip_start;
+    const uint32_t mip_c = mip > c->L ? c->L : mip;
+    const uint64_t guard = 4ull * (c->W + c->H) + 64;
+    const uint32_t steps = o.max_steps ? o.max_steps : (uint32_t)(guard > 0x7FFFFFFF ? 0x7FFFFFFF : guard);
+    if (steps > 0x7FFFFFFFu) return HF_E_INVALID_ARG;
+    Batch b;
+    int rc = prepare_batch(c, cams, n, outs, tw, th, (o.flags & HF_NOWAIT) != 0, o.cuda_stream, b);
+    if (rc != HF_OK) return rc;
+    Slot &s = c->slots[b.slot];
+    hf::RenderParams &p = b.p;
     p.mip_start = (int32_t)mip_c;
     p.shadow_mip = (int32_t)(mip_c + hf::kShadowMipExtra > c->L ? c->L : mip_c + hf::kShadowMipExtra);
     p.max_steps = (int32_t)steps;
@@ -618,38 +648,52 @@ int hf_render(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_outputs *ou
         p.sun[i] = sun[i];
         p.sun_n[i] = (float)(sun[i] / sn);
     }
-
-    if (stream != c->stream) CK(cudaStreamWaitEvent(stream, c->edit_done, 0));
     if (o.flags & HF_PLAIN) {
-        CK(cudaMemcpyAsync(s.d_scratch, s.h_staging, bytes, cudaMemcpyHostToDevice, stream));
+        CK(cudaMemcpyAsync(s.d_scratch, s.h_staging, b.bytes, cudaMemcpyHostToDevice, b.stream));
         for (uint32_t i = 0; i < n; ++i)
-            if (hf::launch_trace_plain(p, shadows, stats, i, tiles[i], stream)) return HF_E_CUDA;
+            if (hf::launch_trace_plain(p, shadows, stats, i, b.tiles[i], b.stream)) return HF_E_CUDA;
     } else if (o.flags & HF_NOGRAPH) {
-        CK(cudaMemcpyAsync(s.d_scratch, s.h_staging, bytes, cudaMemcpyHostToDevice, stream));
+        CK(cudaMemcpyAsync(s.d_scratch, s.h_staging, b.bytes, cudaMemcpyHostToDevice, b.stream));
         if (hf::launch_trace_batched(p, shadows, stats, c->sm_count * c->occ[shadows][stats],
-                                     stream))
+                                     b.stream))
             return HF_E_CUDA;
     } else {
         GraphKey key{};
-        key.bytes = (uint32_t)bucket;
+        key.bytes = (uint32_t)b.bucket;
         key.shadows = shadows;
         key.stats = stats;
-        key.twl = (uint32_t)twl;
-        key.thl = (uint32_t)thl;
+        key.twl = (uint32_t)p.tile_w_log2;
+        key.thl = (uint32_t)p.tile_h_log2;
         key.mip = mip_c;
         key.steps = steps;
         for (int i = 0; i < 3; ++i) key.sun[i] = sun[i];
-        rc = launch_graph(c, s, key, p, shadows, stats, stream);
+        rc = launch_graph(c, s, key, p, shadows, stats, b.stream);
         if (rc != HF_OK) return rc;
     }
-    CK(cudaEventRecord(s.done, stream));
-    s.pending = true;
-    if (o.flags & HF_SYNC) {
-        CK(cudaEventSynchronize(s.done));
-        s.pending = false;
-        return read_status(c);
-    }
-    return HF_OK;
+    return finish_batch(c, b, (o.flags & HF_SYNC) != 0);
+}
+
+int hf_render_march(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_outputs *outs,
+                    const hf_march_opts *opts) {
+    if (!c) return HF_E_INVALID_ARG;
+    if (n == 0) return HF_OK;
+    if (!cams || !outs || n > HF_MAX_CAMERAS) return HF_E_INVALID_ARG;
+    hf_march_opts o{};
+    if (opts) o = *opts;
+    hf::MarchParams m;
+    m.steps = (int32_t)(o.steps ? o.steps : 128);
+    m.bisections = (int32_t)(o.bisections ? o.bisections : 4);
+    m.far_dist = o.far_dist != 0.0f ? o.far_dist : 600.0f;
+    if (o.steps > 65536 || o.bisections > 65536 || !(m.far_dist > 0.0f)) return HF_E_INVALID_ARG;
+    const uint32_t tw = o.tile_w ? o.tile_w : 8, th = o.tile_h ? o.tile_h : 4;
+    if (c->occ_march < 1) return HF_E_CUDA;
+    Batch b;
+    int rc = prepare_batch(c, cams, n, outs, tw, th, false, o.cuda_stream, b);
+    if (rc != HF_OK) return rc;
+    Slot &s = c->slots[b.slot];
+    CK(cudaMemcpyAsync(s.d_scratch, s.h_staging, b.bytes, cudaMemcpyHostToDevice, b.stream));
+    if (hf::launch_march_batched(b.p, m, c->sm_count * c->occ_march, b.stream)) return HF_E_CUDA;
+    return finish_batch(c, b, (o.flags & HF_SYNC) != 0);
 }
 
 }  // extern "C"

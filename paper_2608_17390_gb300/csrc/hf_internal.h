@@ -71,6 +71,15 @@ struct RenderParams {
     float sun_n[3];                // sun / |sun|
 };
 
+// Parameters of the fixed-step comparison marcher (hf_march.cu).
+struct MarchParams {
+    int32_t steps;       // forward samples over the clipped segment
+    int32_t bisections;  // halvings of the bracketing interval
+    float far_dist;      // world units
+};
+int launch_march_batched(const RenderParams &p, const MarchParams &m, int blocks, void *stream);
+int march_occupancy(int *blocks_per_sm);
+
 // Launch wrappers (hf_trace.cu)
 int launch_trace_batched(const RenderParams &p, bool shadows, bool stats, int blocks,
                          void *stream);

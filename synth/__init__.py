@@ -37,6 +37,8 @@ from .cameras import (
     config_c4,
     config_c4_frames,
     small_c2,
+    protocol_cameras,
+    PROTOCOL_PITCHES,
 )
 
 from .requests import poisson_requests, SERVING_RESOLUTIONS
@@ -47,5 +49,6 @@ __all__ = [
     "crater_edit",
     "CAMERA_DTYPE", "pose_to_camera", "ray_camera", "camera_array",
     "config_c1", "config_c2", "config_c3", "c3_cameras", "config_c4", "config_c4_frames",
-    "small_c2", "poisson_requests", "SERVING_RESOLUTIONS",
+    "small_c2", "poisson_requests", "SERVING_RESOLUTIONS", "protocol_cameras",
+    "PROTOCOL_PITCHES",
 ]

@@ -204,3 +204,26 @@ def config_c4_frames(cells, n_frames=1000, w=1920, h=1080, hfov=90.0, seed=4):
         yaw = math.degrees(math.atan2(tan[0], tan[1]))
         cams.append(pose_to_camera(x, y, z, yaw, -10.0, hfov, w, h))
     return camera_array(cams)
+
+
+PROTOCOL_PITCHES = (0.0, -30.0, -60.0, -90.0)
+PROTOCOL_HEIGHT = {0.0: 6.0, -30.0: 60.0, -60.0: 120.0, -90.0: 200.0}
+
+
+def protocol_cameras(cells, seed=12, w=1280, h=800, hfov=75.0, per_pitch=3):
+    """The paper's protocol shape (its Section 4.3): three viewpoints at each
+    pitch 0, -30, -60, -90 deg, 1280 x 800.  Positions and yaws are seeded
+    over the grid (the paper's own viewpoints are locations in its level);
+    each camera sits at a pitch-dependent height above its cell's top
+    (6, 60, 120, 200 units); hfov 75 deg."""
+    H, W = cells.shape
+    cams = []
+    for p_i, pitch in enumerate(PROTOCOL_PITCHES):
+        for v in range(per_pitch):
+            k = 3 * (per_pitch * p_i + v)
+            x = 64.0 + float(unit_float(seed, 9, k)) * (W - 128)
+            y = 64.0 + float(unit_float(seed, 9, k + 1)) * (H - 128)
+            yaw = 360.0 * float(unit_float(seed, 9, k + 2))
+            z = _top(cells, x, y) + PROTOCOL_HEIGHT[pitch]
+            cams.append(pose_to_camera(x, y, z, yaw, pitch, hfov, w, h))
+    return camera_array(cams)
