@@ -41,6 +41,14 @@ def _peaks():
         return HBM_FALLBACK, "fallback"
 
 
+def _peak_sm_mhz():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        return 2070.0
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -61,6 +69,39 @@ def trace_source_hash():
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
+
+
+def _profile_fields(workload):
+    path = os.path.join(ROOT, "profiles", "trace_batched_%s.md" % workload)
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    if fields.get("kernel_source_sha256") != trace_source_hash():
+        return None
+    return fields
+
+
+def _alu_roofline(workload, rays, render_ms, tile, mip, sm_count, sm_mhz):
+    """Instruction-issue roofline of the trace kernel: warp instructions per
+    primary ray (ncu, full-size launch of the same source and launch
+    configuration) times this launch's rays, over the live render time,
+    against SMs x 4 schedulers x 1 instruction/cycle x the SM clock."""
+    f = _profile_fields(workload)
+    if not f or f.get("launch_tile") != tile or f.get("launch_mip_start") != str(mip):
+        return None
+    try:
+        per_ray = float(f["warp_instructions_per_primary_ray"])
+    except (KeyError, ValueError):
+        return None
+    achieved = per_ray * rays / (render_ms / 1e3) / 1e12
+    peak = sm_count * 4 * sm_mhz * 1e6 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T warp-instr/s",
+            "frac": achieved / peak,
+            "peak_source": "%d SMs x 4 schedulers x 1 instr/cycle x %.0f MHz" % (sm_count, sm_mhz)}
 
 
 def _profiled_traffic(workload, rays, scale):
@@ -402,6 +443,9 @@ def run_hf(args):
                      "note": "algorithmic bytes = 4 B x (pyramid nodes + cells + shadow-ray "
                              "fetches, counted in-kernel) + %d B output per ray; most fetches "
                              "are L2/L1 hits" % (14 + (1 if wl["shadows"] else 0))},
+        "alu_roofline": _alu_roofline(args.workload, rays, r_ms, "%dx%d" % (tile_w, tile_h),
+                                      mip_start, info["sm_count"],
+                                      (ck or {}).get("sm_mhz") or _peak_sm_mhz()),
         "fetches_per_ray": (st["node_fetches"] + st["cell_fetches"]) / max(rays, 1),
         "gpu_launches": args.steps * ((2 if wl["edit"] else 1)),
         "clocks": ck,
