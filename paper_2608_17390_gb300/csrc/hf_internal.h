@@ -20,10 +20,16 @@ constexpr int kThreads = 128;   // threads per trace block (4 warps)
 constexpr uint32_t kMaxCams = 4096;
 constexpr uint32_t kDefaultMipStart = 6;  // coarsest level used when the caller asks for the default
 #ifndef HF_SHADOW_MIP_EXTRA
-#define HF_SHADOW_MIP_EXTRA 0
+#define HF_SHADOW_MIP_EXTRA 4
 #endif
-// shadow rays start this many levels higher (they rise above the terrain and travel far)
+// shadow rays may climb this many levels higher than primary rays
 constexpr uint32_t kShadowMipExtra = HF_SHADOW_MIP_EXTRA;
+#ifndef HF_SHADOW_START
+#define HF_SHADOW_START 0
+#endif
+// level at which a shadow ray starts: its origin lies next to a surface, so
+// the coarse nodes around it are rarely empty; it climbs as it leaves them
+constexpr int kShadowStart = HF_SHADOW_START;
 
 constexpr uint8_t kFaceNX = 0, kFacePX = 1, kFaceNY = 2, kFacePY = 3, kFaceNZ = 4, kFacePZ = 5,
                   kFaceInside = 6, kFaceError = 254, kFaceMiss = 255;

@@ -194,8 +194,8 @@ __device__ __forceinline__ bool vertical_test(const Ray &r, uint32_t word, Hit &
 // its Y side while also crossing an X cell boundary (a corner) is detected on
 // the way down and reported with the X face.
 template <bool STATS>
-__device__ __forceinline__ void trace_ray(const WorldDev &w, const Ray &r, int mip_start,
-                                          int max_steps, Hit &h, Counters &cnt) {
+__device__ __forceinline__ void trace_ray(const WorldDev &w, const Ray &r, int start_level,
+                                          int mip_start, int max_steps, Hit &h, Counters &cnt) {
     h.face = kFaceMiss;
     h.layer = 255;
     const int sx = (r.dx > 0) - (r.dx < 0), sy = (r.dy > 0) - (r.dy < 0);
@@ -216,7 +216,7 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const Ray &r, int m
         return;
     }
 
-    int level = mip_start;
+    int level = start_level;  // <= mip_start, the coarsest level the ray climbs to
     int32_t nx = cx >> level, ny = cy >> level;
     int32_t tin_num = 0, tin_den = 1;
     uint8_t entry = kFaceInside;
@@ -350,9 +350,9 @@ __device__ __forceinline__ void store_pixel(const RenderParams &p, const CamDev 
 // One pixel: its primary ray, then (with shadows) the shadow ray, which
 // reuses the same traversal loop and registers.
 template <bool SHADOWS, bool STATS>
-__device__ __forceinline__ void trace_pixel(const RenderParams &p, const CamDev &c, int32_t px,
-                                            int32_t py, Counters &cnt, Counters &scnt,
-                                            uint32_t &nshadow, bool &err) {
+__device__ __forceinline__ void trace_pixel(const RenderParams &p, const CamDev &c, int start,
+                                            int32_t px, int32_t py, Counters &cnt,
+                                            Counters &scnt, uint32_t &nshadow, bool &err) {
     const int32_t a = 2 * px + 1 - (int32_t)c.w;
     const int32_t b = (int32_t)c.h - 1 - 2 * py;
     Ray r;
@@ -369,9 +369,10 @@ __device__ __forceinline__ void trace_pixel(const RenderParams &p, const CamDev 
     for (;;) {
         Hit h;
         if (!SHADOWS || !shadow_pass) {
-            trace_ray<STATS>(p.world, r, p.mip_start, p.max_steps, h, cnt);
+            trace_ray<STATS>(p.world, r, start, p.mip_start, p.max_steps, h, cnt);
         } else {
-            trace_ray<STATS>(p.world, r, p.shadow_mip, p.max_steps, h, scnt);
+            trace_ray<STATS>(p.world, r, min(kShadowStart, p.shadow_mip), p.shadow_mip,
+                             p.max_steps, h, scnt);
         }
         if (h.face == kFaceError) err = true;
         if (SHADOWS && shadow_pass) {
@@ -415,6 +416,29 @@ __device__ __forceinline__ void trace_pixel(const RenderParams &p, const CamDev 
     store_pixel(p, c, (uint32_t)py * c.w + (uint32_t)px, ph, depth, visible, SHADOWS);
 }
 
+// Start level of a camera's primary rays: the largest level l <= mip_start
+// whose node around the camera cell has every top below the camera, but not
+// below level min(2, mip_start) (a measured floor: climbing out of levels 0
+// and 1 costs more steps than the two descents it saves).  Node tops only
+// grow with the level, so the levels under the camera are 0..l; lane k tests
+// level k.  A camera outside the grid starts at mip_start.  The traversal is
+// exact from any start level (a ray climbs as it crosses parent boundaries);
+// the rule only saves descents through nodes around the camera that cannot
+// be empty.
+__device__ __forceinline__ int primary_start(const RenderParams &p, const CamDev &c, int lane) {
+    const WorldDev &w = p.world;
+    const int32_t cx = c.o[0] >> kShift, cy = c.o[1] >> kShift;
+    if ((uint32_t)cx >= (uint32_t)w.W || (uint32_t)cy >= (uint32_t)w.H) return p.mip_start;
+    bool above = false;
+    if (lane <= p.mip_start) {
+        const uint32_t word = load_word(w, lane, cx >> lane, cy >> lane);
+        const int32_t top = ((lane > 0 ? word : cell_as_node(word)) >> 16) & 0xFF;
+        above = c.o[2] > (top << kShift);
+    }
+    const uint32_t mask = __ballot_sync(0xFFFFFFFFu, above);
+    return max(min(2, p.mip_start), __ffs(~mask) - 2);
+}
+
 // One warp renders one tile: lane l traces the tile's pixels l, l+32, ...
 template <bool SHADOWS, bool STATS>
 __device__ __forceinline__ void trace_tile(const RenderParams &p, const CamDev &c,
@@ -426,11 +450,12 @@ __device__ __forceinline__ void trace_tile(const RenderParams &p, const CamDev &
     Counters cnt{0, 0}, scnt{0, 0};
     uint32_t nshadow = 0, nrays = 0;
     bool err = false;
+    const int start = primary_start(p, c, lane);
     for (int i = lane; i < npix; i += 32) {
         const int32_t px = x0 + (i & ((1 << tw_log2) - 1));
         const int32_t py = y0 + (i >> tw_log2);
         if (px < (int32_t)c.w && py < (int32_t)c.h) {
-            trace_pixel<SHADOWS, STATS>(p, c, px, py, cnt, scnt, nshadow, err);
+            trace_pixel<SHADOWS, STATS>(p, c, start, px, py, cnt, scnt, nshadow, err);
             if (STATS) nrays++;
         }
     }

@@ -52,12 +52,13 @@ def test_alu_roofline_only_for_the_profiled_launch():
     import bench
 
     f = bench._profile_fields("c3")
-    r = bench._alu_roofline("c3", 188006400, 30.0, "8x16", 6, 152, 2070.0)
     if f is None:
-        assert r is None
+        assert bench._alu_roofline("c3", 188006400, 30.0, "8x16", 6, 152, 2070.0) is None
         return
+    tile, mip = f["launch_tile"], int(f["launch_mip_start"])
+    r = bench._alu_roofline("c3", 188006400, 30.0, tile, mip, 152, 2070.0)
     assert r["bound"] == "alu" and 0 < r["frac"] < 1.5
     assert r["peak"] == pytest.approx(152 * 4 * 2070e6 / 1e12)
-    tile = f["launch_tile"]
     other = "4x8" if tile != "4x8" else "8x4"
-    assert bench._alu_roofline("c3", 188006400, 30.0, other, 6, 152, 2070.0) is None
+    assert bench._alu_roofline("c3", 188006400, 30.0, other, mip, 152, 2070.0) is None
+    assert bench._alu_roofline("c3", 188006400, 30.0, tile, mip + 1, 152, 2070.0) is None

@@ -253,6 +253,45 @@ def test_edge_cases(hf):
             hf.hf_destroy(ctx)
 
 
+def test_camera_heights_at_node_tops_and_in_caves(hf):
+    """Cameras exactly at a pyramid node's top height, one 2^-16 unit above
+    it, inside a slab cave, on an exact cell corner, and on the grid's corner
+    looking out (origins outside the grid are rejected by validation):
+    the level a camera's rays start from depends on these comparisons, and
+    every start must give the oracle's image at every mip."""
+    rng = np.random.default_rng(2024)
+    cells = _rand_grid(rng, 96, 80, hmax=40)
+    levels = oracle.pyramid(cells)  # levels 1..L, byte 2 = max top
+    poses = []
+    for k, (x, y) in enumerate([(40.0, 33.0), (10.5, 70.25), (77.0, 12.0)]):
+        cx, cy = int(x), int(y)
+        h0, h1, h2, _ = synth.unpack_cells(cells[cy, cx])
+        top0 = int(h2) if int(h1) > int(h0) else int(h0)
+        tops = [top0] + [int((lv[cy >> (i + 1), cx >> (i + 1)] >> 16) & 0xFF)
+                         for i, lv in enumerate(levels)]
+        for lvl in (0, 2, 4):
+            for dz in (0.0, 1.0 / 65536):
+                poses.append(synth.pose_to_camera(x, y, tops[lvl] + dz, 97.0 * k + 31 * lvl,
+                                                  -20.0 + 10 * lvl, 80, 23, 11))
+    cave = np.argwhere((synth.unpack_cells(cells)[1] > synth.unpack_cells(cells)[0] + 1))[0]
+    h0, h1, _, _ = synth.unpack_cells(cells[cave[0], cave[1]])
+    poses.append(synth.pose_to_camera(cave[1] + 0.5, cave[0] + 0.5, (int(h0) + int(h1)) / 2.0,
+                                      200, 5, 90, 31, 9))
+    poses.append(synth.pose_to_camera(0.0, 0.0, 50.0, 225, -30, 70, 27, 13))
+    poses.append(synth.pose_to_camera(48.0, 40.0, 45.0, 225, -45, 70, 27, 13))
+    cams = synth.camera_array(poses)
+    ctx = _ctx(hf, cells)
+    try:
+        orc = [oracle.render(cells, c, shadows=True) for c in cams]
+        for mip in (0, 1, 3, 5, 7):
+            g = gpu_render(hf, ctx, cams, shadows=True,
+                           opts=hf.make_opts(mip_start=mip, flags=hf.HF_SHADOWS))
+            for i in range(len(cams)):
+                compare(g[i], orc[i], shadows=True, what="cam %d mip %d" % (i, mip))
+    finally:
+        hf.hf_destroy(ctx)
+
+
 def test_vertical_rays_hit_height_zero(hf):
     """Odd image sizes put a pixel exactly on the optical axis: with pitch -90
     that ray is vertical; height zero must be hit from above (the paper's
