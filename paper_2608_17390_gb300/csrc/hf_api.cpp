@@ -287,6 +287,8 @@ static int create_impl(const hf_desc *d, hf_ctx *c) {
     const size_t stride = d->row_stride ? d->row_stride : d->width;
     CK(cudaMemcpy2DAsync(c->d_world, (size_t)c->W * 4, d->cells, stride * 4, (size_t)c->W * 4,
                          c->H, cudaMemcpyHostToDevice, c->stream));
+    // level 0 is kept in node form (hf::cell_encode)
+    if (hf::cells_encode(c->d_world, c->W * c->H, c->stream)) return HF_E_CUDA;
     if (hf::pyramid_build(c->d_world, c->wd, c->stream)) return HF_E_CUDA;
     if (cudaMalloc(&c->d_status, sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc(&c->d_stats, 5 * sizeof(unsigned long long)) != cudaSuccess ||
@@ -372,8 +374,11 @@ int hf_edit(hf_ctx *c, uint32_t x0, uint32_t y0, uint32_t w, uint32_t h, const u
         }
         c->edit_cap = cap;
     }
-    for (uint32_t y = 0; y < h; ++y)
-        std::memcpy(c->h_edit + (size_t)y * w, cells + (size_t)y * stride, (size_t)w * 4);
+    for (uint32_t y = 0; y < h; ++y) {  // staged in node form (hf::cell_encode)
+        const uint32_t *src = cells + (size_t)y * stride;
+        uint32_t *dst = c->h_edit + (size_t)y * w;
+        for (uint32_t x = 0; x < w; ++x) dst[x] = hf::cell_encode(src[x]);
+    }
     // no in-flight render may observe the edit
     for (auto &s : c->slots)
         if (s.pending) CK(cudaStreamWaitEvent(c->stream, s.done, 0));
@@ -417,6 +422,10 @@ int hf_read_cells(hf_ctx *c, uint32_t x0, uint32_t y0, uint32_t w, uint32_t h, u
     CK(cudaMemcpy2DAsync(out, stride * 4, c->d_world + (size_t)y0 * c->W + x0, (size_t)c->W * 4,
                          (size_t)w * 4, h, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    for (uint32_t y = 0; y < h; ++y) {  // back from node form
+        uint32_t *row = out + (size_t)y * stride;
+        for (uint32_t x = 0; x < w; ++x) row[x] = hf::cell_decode(row[x]);
+    }
     return HF_OK;
 }
 

@@ -1,18 +1,36 @@
 // hf_internal.h -- device-side structures shared by the kernels and the C ABI.
 //
 // Memory layout in HBM (one allocation per context, 256-byte aligned levels):
-//   level 0   : the cells, W x H uint32 words, row-major y*W + x
+//   level 0   : the cells, W x H uint32 words, row-major y*W + x, each in node
+//               form with its material (cell_encode below)
 //   level k>=1: ceil(W/2^k) x ceil(H/2^k) node words, row-major,
 //               byte0 max h0, byte1 min (slab ? h1 : 255), byte2 max (slab ? h2 : h0)
 // Per-render scratch (one block per render slot):
 //   BatchHeader (tile counter, camera count, tile count), then CamDev[n].
 #pragma once
 
+#include <cuda_runtime.h>
 #include <cstdint>
 
 struct hf_ctx;  // the C ABI's opaque context (hf_api.cpp)
 
 namespace hf {
+
+// A valid cell word (byte0 h0, byte1 h1, byte2 h2, byte3 material; a slab
+// when h1 > h0, else h1 = h2 = 0) in the node form of a one-cell pyramid
+// node: byte0 h0, byte1 (slab ? h1 : 255), byte2 (slab ? h2 : h0), material
+// kept in byte3.  Slab cells are unchanged; the map is one to one on valid
+// cells (a slab exactly when byte2 > byte0), so level 0 is stored this way
+// and every traversal level reads the same word layout.
+__host__ __device__ inline uint32_t cell_encode(uint32_t c) {
+    const uint32_t h0 = c & 0xFF, h1 = (c >> 8) & 0xFF;
+    return h1 > h0 ? c : (c & 0xFF0000FFu) | 0xFF00u | (h0 << 16);
+}
+// Inverse of cell_encode.
+__host__ __device__ inline uint32_t cell_decode(uint32_t n) {
+    const uint32_t b0 = n & 0xFF, b2 = (n >> 16) & 0xFF;
+    return b2 > b0 ? n : (n & 0xFF0000FFu);
+}
 
 constexpr int kMaxLevels = 14;  // 2^14 = 16384 = largest grid side
 constexpr int kShift = 16;      // 2^16 fixed-point units per world unit
@@ -111,6 +129,8 @@ int pyramid_repair(uint32_t *world, const WorldDev &w, int32_t x0, int32_t y0, i
 // Same, for levels k_from..L only (levels below k_from must already be current).
 int pyramid_repair_from(uint32_t *world, const WorldDev &w, int k_from, int32_t x0, int32_t y0,
                         int32_t x1, int32_t y1, void *stream);
+// Encode the W x H cells just copied to level 0 into node form, in place.
+int cells_encode(uint32_t *cells, uint32_t n, void *stream);
 // Full build of levels 1..L from the cells: levels 1..6 by 64 x 64 tiles in
 // shared memory (cells read once), the rest by repair of the whole grid.
 int pyramid_build(uint32_t *world, const WorldDev &w, void *stream);

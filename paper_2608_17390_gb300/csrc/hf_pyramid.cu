@@ -22,10 +22,13 @@ constexpr uint32_t kIdentity = 0x0000FF00u;  // max h0 0, min h1 255, max top 0
 constexpr int64_t kTailNodes = 4096;         // below this, finish in one block
 constexpr int kTailThreads = 512;
 
-__device__ __forceinline__ uint32_t cell_node(uint32_t c) {
-    const uint32_t h0 = c & 0xFF, h1 = (c >> 8) & 0xFF, h2 = (c >> 16) & 0xFF;
-    const bool slab = h1 > h0;
-    return h0 | ((slab ? h1 : 255u) << 8) | ((slab ? h2 : h0) << 16);
+// Level-0 words are stored in node form (cell_encode); the node of one cell
+// is its word without the material byte.
+__device__ __forceinline__ uint32_t cell_node(uint32_t c) { return c & 0x00FFFFFFu; }
+
+__global__ void k_cells_encode(uint32_t *__restrict__ cells, uint32_t n) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        cells[i] = cell_encode(cells[i]);
 }
 
 // byte0 and byte2 by max, byte1 by min (each field compared in place)
@@ -174,6 +177,13 @@ __global__ void __launch_bounds__(kBuildThreads) k_pyr_build_tiles(uint32_t *wor
 }
 
 }  // namespace
+
+int cells_encode(uint32_t *cells, uint32_t n, void *stream) {
+    if (n == 0) return 0;
+    const uint32_t blocks = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+    k_cells_encode<<<blocks, 256, 0, (cudaStream_t)stream>>>(cells, n);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
 
 int pyramid_build(uint32_t *world, const WorldDev &w, void *stream) {
     cudaStream_t s = (cudaStream_t)stream;

@@ -81,23 +81,13 @@ __device__ __forceinline__ uint32_t load_word(const WorldDev &w, int level, int3
     return __ldg(w.base + w.off[level] + (uint32_t)y * w.stride[level] + (uint32_t)x);
 }
 
-// A cell word in pyramid-node form: max h0, min (slab ? h1 : 255), max top.
-// For one cell the node emptiness test is exact: the segment's z range
-// [zlo, zhi] misses (-inf, h0] and [h1, h2] exactly when zlo > top, or
-// zlo > h0 and zhi < h1.
-__device__ __forceinline__ uint32_t cell_as_node(uint32_t c) {
-    const uint32_t h0 = c & 0xFF, h1 = (c >> 8) & 0xFF, h2 = (c >> 16) & 0xFF;
-    const bool slab = h1 > h0;
-    return h0 | ((slab ? h1 : 255u) << 8) | ((slab ? h2 : h0) << 16);
-}
-
 // The two-interval test of one cell over [tin, tout] (tout finite).
 // Returns true and fills h on a hit.
 __device__ __forceinline__ bool leaf_test(const Ray &r, uint32_t word, int32_t tin_num,
                                           int32_t tin_den, int32_t tout_num, int32_t tout_den,
                                           uint8_t entry_face, Hit &h) {
     const int32_t h0 = word & 0xFF, h1 = (word >> 8) & 0xFF, h2 = (word >> 16) & 0xFF;
-    const bool slab = h1 > h0;
+    const bool slab = h2 > h0;  // level-0 words are in node form
     const int32_t a0 = r.oz - (h0 << kShift);
     const int64_t zin0 = zd(a0, r.dz, tin_num, tin_den);
     if (zin0 <= 0) {
@@ -151,7 +141,7 @@ __device__ __forceinline__ bool leaf_test(const Ray &r, uint32_t word, int32_t t
 // Writes h only when the ray hits.
 __device__ __forceinline__ bool vertical_test(const Ray &r, uint32_t word, Hit &h) {
     const int32_t h0 = word & 0xFF, h1 = (word >> 8) & 0xFF, h2 = (word >> 16) & 0xFF;
-    const bool slab = h1 > h0;
+    const bool slab = h2 > h0;  // level-0 words are in node form
     const int32_t a0 = r.oz - (h0 << kShift), a1 = r.oz - (h1 << kShift),
                   a2 = r.oz - (h2 << kShift);
     uint8_t layer, face;
@@ -230,8 +220,12 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const Ray &r, int s
         const bool xfirst = cmp <= 0;
         const int32_t tout_num = xfirst ? numx : numy;
         const int32_t tout_den = xfirst ? adx : ady;
+        // level 0 holds cells in node form, so one word layout serves every
+        // level; for a single cell the emptiness test below is exact (the
+        // segment's z range [zlo, zhi] misses (-inf, h0] and [h1, h2] exactly
+        // when zlo > top, or zlo > h0 and zhi < h1)
         const uint32_t word = load_word(w, level, nx, ny);
-        const uint32_t node = level > 0 ? word : cell_as_node(word);
+        const uint32_t node = word;
         if (STATS) {
             if (level > 0) cnt.nodes++;
             else cnt.cells++;
@@ -432,7 +426,7 @@ __device__ __forceinline__ int primary_start(const RenderParams &p, const CamDev
     bool above = false;
     if (lane <= p.mip_start) {
         const uint32_t word = load_word(w, lane, cx >> lane, cy >> lane);
-        const int32_t top = ((lane > 0 ? word : cell_as_node(word)) >> 16) & 0xFF;
+        const int32_t top = (word >> 16) & 0xFF;  // every level in node form
         above = c.o[2] > (top << kShift);
     }
     const uint32_t mask = __ballot_sync(0xFFFFFFFFu, above);

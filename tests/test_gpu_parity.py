@@ -317,6 +317,47 @@ def _pyr_equal(hf, ctx, cells, what):
         assert got.shape == lv.shape and (got == lv).all(), "%s level %d" % (what, k)
 
 
+def _extreme_cells(rng, W, H):
+    """Valid cells at the ends of every byte range: no slab at h0 = 0 and 255,
+    slabs [h0+1, 255], [255, 255], [1, 1] over h0 = 0, materials 0 and 255."""
+    kinds = [(0, 0, 0), (255, 0, 0), (254, 255, 255), (0, 1, 1), (0, 255, 255), (7, 8, 200),
+             (100, 0, 0)]
+    k = rng.integers(0, len(kinds), (H, W))
+    h0 = np.array([t[0] for t in kinds])[k]
+    h1 = np.array([t[1] for t in kinds])[k]
+    h2 = np.array([t[2] for t in kinds])[k]
+    mat = rng.choice([0, 1, 128, 255], (H, W))
+    return synth.pack_cells(h0, h1, h2, mat)
+
+
+def test_cells_read_back_unchanged_at_byte_extremes(hf):
+    """The device keeps its own cell layout; what goes in through hf_create and
+    hf_edit comes back unchanged through hf_read_cells, and the pyramid and
+    renders see the same cells as the oracle."""
+    rng = np.random.default_rng(255)
+    W, H = 77, 45
+    cells = _extreme_cells(rng, W, H)
+    assert hf.hf_validate_cells(cells)[0] == hf.HF_OK
+    ctx = _ctx(hf, cells)
+    try:
+        assert (hf.hf_read_cells(ctx, 0, 0, W, H) == cells).all()
+        blk = _extreme_cells(rng, 20, 9)
+        hf.hf_edit(ctx, 50, 30, blk)
+        cells[30:39, 50:70] = blk
+        hf.hf_sync(ctx)
+        assert (hf.hf_read_cells(ctx, 0, 0, W, H) == cells).all()
+        assert (hf.hf_read_cells(ctx, 49, 29, 13, 7) == cells[29:36, 49:62]).all()
+        _pyr_equal(hf, ctx, cells, "extremes")
+        cams = synth.camera_array([synth.pose_to_camera(38.5, 22.5, 300.0, 30, -70, 80, 41, 23),
+                                   synth.pose_to_camera(10.5, 5.5, 120.0, 60, -10, 90, 41, 23)])
+        g = gpu_render(hf, ctx, cams, shadows=True, opts=hf.make_opts(flags=hf.HF_SHADOWS))
+        for i, c in enumerate(cams):
+            compare(g[i], oracle.render(cells, c, shadows=True), shadows=True,
+                    what="extremes cam %d" % i)
+    finally:
+        hf.hf_destroy(ctx)
+
+
 def test_pyramid_build_and_repair_equal_rebuild(hf):
     rng = np.random.default_rng(3)
     for W, H in ((300, 200), (64, 64), (1, 70), (129, 3)):
