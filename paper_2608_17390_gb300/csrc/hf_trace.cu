@@ -188,7 +188,6 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const Ray &r, int s
                                           int mip_start, int max_steps, Hit &h, Counters &cnt) {
     h.face = kFaceMiss;
     h.layer = 255;
-    const int sx = (r.dx > 0) - (r.dx < 0), sy = (r.dy > 0) - (r.dy < 0);
     const int32_t adx = abs(r.dx), ady = abs(r.dy);
     int32_t cx = r.ox >> kShift, cy = r.oy >> kShift;
     if (r.dx < 0 && (r.ox & 0xFFFF) == 0) cx -= 1;
@@ -206,16 +205,24 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const Ray &r, int s
         return;
     }
 
+    // Per-ray sign constants.  A zero direction component counts as positive:
+    // its exit distance is then positive and never the smaller one, so the
+    // ray never leaves through that axis.
+    const int32_t gx = r.dx < 0 ? -1 : 1, gy = r.dy < 0 ? -1 : 1;  // step per exit
+    const int32_t px = r.dx < 0 ? 0 : 1, py = r.dy < 0 ? 0 : 1;    // exit side offset
+    const int32_t kx = -gx * r.ox, ky = -gy * r.oy;
+    const uint8_t face_x = r.dx < 0 ? kFacePX : kFaceNX;  // entry face of an x crossing
+    const uint8_t face_y = r.dy < 0 ? kFacePY : kFaceNY;
     int level = start_level;  // <= mip_start, the coarsest level the ray climbs to
     int32_t nx = cx >> level, ny = cy >> level;
     int32_t tin_num = 0, tin_den = 1;
     uint8_t entry = kFaceInside;
 
     for (int it = 0; it < max_steps; ++it) {
-        const int32_t bx = (sx > 0 ? nx + 1 : nx) << level;  // exit boundary (cells)
-        const int32_t by = (sy > 0 ? ny + 1 : ny) << level;
-        const int32_t numx = sx > 0 ? (bx << kShift) - r.ox : (sx < 0 ? r.ox - (bx << kShift) : 1);
-        const int32_t numy = sy > 0 ? (by << kShift) - r.oy : (sy < 0 ? r.oy - (by << kShift) : 1);
+        const int32_t bx = (nx + px) << level;  // exit boundary (cells)
+        const int32_t by = (ny + py) << level;
+        const int32_t numx = gx * (bx << kShift) + kx;  // > 0
+        const int32_t numy = gy * (by << kShift) + ky;
         const int64_t cmp = (int64_t)numx * ady - (int64_t)numy * adx;  // < 0: x exits first
         const bool xfirst = cmp <= 0;
         const int32_t tout_num = xfirst ? numx : numy;
@@ -240,30 +247,20 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const Ray &r, int s
                             zd(r.oz - (minh1 << kShift), r.dz, hi_num, hi_den) < 0);
         if (!empty) {
             if (level > 0) {
-                // descend into the child that holds the ray just after t_in
+                // descend into the child that holds the ray just after t_in:
+                // the upper child on an axis when the ray has passed that
+                // axis' midline by t_in (for a negative direction, when not)
                 --level;
                 const int32_t xm = (2 * nx + 1) << level, ym = (2 * ny + 1) << level;
-                bool on_x = false;
-                if (sx != 0) {
-                    const int64_t lhs =
-                        (int64_t)(sx > 0 ? (xm << kShift) - r.ox : r.ox - (xm << kShift)) * tin_den;
-                    const int64_t rhs = (int64_t)tin_num * adx;
-                    const bool past = lhs <= rhs;
-                    on_x = lhs == rhs;
-                    nx = 2 * nx + ((sx > 0) == past ? 1 : 0);
-                } else {
-                    nx = 2 * nx + (r.ox >= (xm << kShift) ? 1 : 0);
-                }
-                if (sy != 0) {
-                    const int64_t lhs =
-                        (int64_t)(sy > 0 ? (ym << kShift) - r.oy : r.oy - (ym << kShift)) * tin_den;
-                    const bool past = lhs <= (int64_t)tin_num * ady;
-                    ny = 2 * ny + ((sy > 0) == past ? 1 : 0);
-                } else {
-                    ny = 2 * ny + (r.oy >= (ym << kShift) ? 1 : 0);
-                }
-                if (on_x && (entry == kFaceNY || entry == kFacePY))
-                    entry = sx > 0 ? kFaceNX : kFacePX;  // a corner: report the X face
+                const int64_t lx = (int64_t)(gx * (xm << kShift) + kx) * tin_den;
+                const int64_t rx = (int64_t)tin_num * adx;
+                const int64_t ly = (int64_t)(gy * (ym << kShift) + ky) * tin_den;
+                const int64_t ry = (int64_t)tin_num * ady;
+                nx = 2 * nx + ((lx <= rx) != (gx < 0) ? 1 : 0);
+                ny = 2 * ny + ((ly <= ry) != (gy < 0) ? 1 : 0);
+                // a corner: the ray enters the cell through its Y side and an
+                // X cell boundary at the same instant; report the X face
+                if (lx == rx && adx != 0 && entry == face_y) entry = face_x;
                 if ((uint32_t)nx >= w.stride[level] || (uint32_t)ny >= w.rows[level]) return;
                 continue;
             }
@@ -275,18 +272,11 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const Ray &r, int s
                 return;
             }
         }
-        // advance past the node (or cell) through its exit side
-        if (cmp < 0) {
-            nx += sx;
-            entry = sx > 0 ? kFaceNX : kFacePX;
-        } else if (cmp > 0) {
-            ny += sy;
-            entry = sy > 0 ? kFaceNY : kFacePY;
-        } else {  // exact corner: both axes change
-            nx += sx;
-            ny += sy;
-            entry = sx > 0 ? kFaceNX : kFacePX;
-        }
+        // advance past the node (or cell) through its exit side; at an exact
+        // corner both indices change and the X face is reported
+        if (cmp <= 0) nx += gx;
+        if (cmp >= 0) ny += gy;
+        entry = cmp <= 0 ? face_x : face_y;
         tin_num = tout_num;
         tin_den = tout_den;
         if ((uint32_t)nx >= w.stride[level] || (uint32_t)ny >= w.rows[level]) return;
