@@ -43,6 +43,13 @@ struct Ray {
     int32_t ox, oy, oz, dx, dy, dz;
 };
 
+// One pyramid level as the traversal reads it (a per-block shared table, so
+// lanes at different levels read it in one shared-memory access).
+struct LevelDev {
+    const uint32_t *base;
+    uint32_t stride, rows;
+};
+
 struct Hit {
     int32_t cx, cy;
     int32_t tnum, tden;  // hit time tnum / tden
@@ -184,8 +191,9 @@ __device__ __forceinline__ bool vertical_test(const Ray &r, uint32_t word, Hit &
 // its Y side while also crossing an X cell boundary (a corner) is detected on
 // the way down and reported with the X face.
 template <bool STATS>
-__device__ __forceinline__ void trace_ray(const WorldDev &w, const Ray &r, int start_level,
-                                          int mip_start, int max_steps, Hit &h, Counters &cnt) {
+__device__ __forceinline__ void trace_ray(const WorldDev &w, const LevelDev *lvt, const Ray &r,
+                                          int start_level, int mip_start, int max_steps, Hit &h,
+                                          Counters &cnt) {
     h.face = kFaceMiss;
     h.layer = 255;
     const int32_t adx = abs(r.dx), ady = abs(r.dy);
@@ -218,6 +226,7 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const Ray &r, int s
     int32_t tin_num = 0, tin_den = 1;
     uint8_t entry = kFaceInside;
 
+
     for (int it = 0; it < max_steps; ++it) {
         const int32_t bx = (nx + px) << level;  // exit boundary (cells)
         const int32_t by = (ny + py) << level;
@@ -231,7 +240,8 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const Ray &r, int s
         // level; for a single cell the emptiness test below is exact (the
         // segment's z range [zlo, zhi] misses (-inf, h0] and [h1, h2] exactly
         // when zlo > top, or zlo > h0 and zhi < h1)
-        const uint32_t word = load_word(w, level, nx, ny);
+        const LevelDev lv = lvt[level];
+        const uint32_t word = __ldg(lv.base + (uint32_t)ny * lv.stride + (uint32_t)nx);
         const uint32_t node = word;
         if (STATS) {
             if (level > 0) cnt.nodes++;
@@ -261,7 +271,7 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const Ray &r, int s
                 // a corner: the ray enters the cell through its Y side and an
                 // X cell boundary at the same instant; report the X face
                 if (lx == rx && adx != 0 && entry == face_y) entry = face_x;
-                if ((uint32_t)nx >= w.stride[level] || (uint32_t)ny >= w.rows[level]) return;
+                if ((uint32_t)nx >= lvt[level].stride || (uint32_t)ny >= lvt[level].rows) return;
                 continue;
             }
             // a non-empty cell holds the hit: find its layer, face and time
@@ -279,13 +289,14 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const Ray &r, int s
         entry = cmp <= 0 ? face_x : face_y;
         tin_num = tout_num;
         tin_den = tout_den;
-        if ((uint32_t)nx >= w.stride[level] || (uint32_t)ny >= w.rows[level]) return;
+        if ((uint32_t)nx >= lv.stride || (uint32_t)ny >= lv.rows) return;
         if (level < mip_start) {  // ascend when the crossed boundary is a parent boundary
             const int32_t bnd = cmp <= 0 ? bx : by;
             if ((bnd & ((2 << level) - 1)) == 0) {
                 ++level;
                 nx >>= 1;
                 ny >>= 1;
+
             }
         }
     }
@@ -334,7 +345,8 @@ __device__ __forceinline__ void store_pixel(const RenderParams &p, const CamDev 
 // One pixel: its primary ray, then (with shadows) the shadow ray, which
 // reuses the same traversal loop and registers.
 template <bool SHADOWS, bool STATS>
-__device__ __forceinline__ void trace_pixel(const RenderParams &p, const CamDev &c, int start,
+__device__ __forceinline__ void trace_pixel(const RenderParams &p, const LevelDev *lvt,
+                                            const CamDev &c, int start,
                                             int32_t px, int32_t py, Counters &cnt,
                                             Counters &scnt, uint32_t &nshadow, bool &err) {
     const int32_t a = 2 * px + 1 - (int32_t)c.w;
@@ -353,9 +365,9 @@ __device__ __forceinline__ void trace_pixel(const RenderParams &p, const CamDev 
     for (;;) {
         Hit h;
         if (!SHADOWS || !shadow_pass) {
-            trace_ray<STATS>(p.world, r, start, p.mip_start, p.max_steps, h, cnt);
+            trace_ray<STATS>(p.world, lvt, r, start, p.mip_start, p.max_steps, h, cnt);
         } else {
-            trace_ray<STATS>(p.world, r, min(kShadowStart, p.shadow_mip), p.shadow_mip,
+            trace_ray<STATS>(p.world, lvt, r, min(kShadowStart, p.shadow_mip), p.shadow_mip,
                              p.max_steps, h, scnt);
         }
         if (h.face == kFaceError) err = true;
@@ -425,8 +437,8 @@ __device__ __forceinline__ int primary_start(const RenderParams &p, const CamDev
 
 // One warp renders one tile: lane l traces the tile's pixels l, l+32, ...
 template <bool SHADOWS, bool STATS>
-__device__ __forceinline__ void trace_tile(const RenderParams &p, const CamDev &c,
-                                           uint32_t local_tile, int lane) {
+__device__ __forceinline__ void trace_tile(const RenderParams &p, const LevelDev *lvt,
+                                           const CamDev &c, uint32_t local_tile, int lane) {
     const uint32_t tx = local_tile % c.tiles_x, ty = local_tile / c.tiles_x;
     const int32_t tw_log2 = p.tile_w_log2;
     const int32_t x0 = (int32_t)tx << tw_log2, y0 = (int32_t)ty << p.tile_h_log2;
@@ -439,7 +451,7 @@ __device__ __forceinline__ void trace_tile(const RenderParams &p, const CamDev &
         const int32_t px = x0 + (i & ((1 << tw_log2) - 1));
         const int32_t py = y0 + (i >> tw_log2);
         if (px < (int32_t)c.w && py < (int32_t)c.h) {
-            trace_pixel<SHADOWS, STATS>(p, c, start, px, py, cnt, scnt, nshadow, err);
+            trace_pixel<SHADOWS, STATS>(p, lvt, c, start, px, py, cnt, scnt, nshadow, err);
             if (STATS) nrays++;
         }
     }
@@ -458,6 +470,11 @@ __device__ __forceinline__ void trace_tile(const RenderParams &p, const CamDev &
             atomicAdd(p.stats + 4, (unsigned long long)vf);
         }
     }
+}
+
+__device__ __forceinline__ void fill_levels(LevelDev *s_lv, const WorldDev &w) {
+    const int k = threadIdx.x;
+    if (k <= w.L) s_lv[k] = LevelDev{w.base + w.off[k], (uint32_t)w.stride[k], (uint32_t)w.rows[k]};
 }
 
 // Copy camera i into this warp's shared slot (fields are then read on demand
@@ -479,9 +496,11 @@ template <bool SHADOWS, bool STATS>
 __global__ void __launch_bounds__(kThreads, HF_TRACE_MIN_BLOCKS) k_trace_batched(const RenderParams p) {
     __shared__ uint32_t s_base[kMaxCams + 1];
     __shared__ CamDev s_cam[kThreads / 32];
+    __shared__ LevelDev s_lv[kMaxLevels + 1];
     const uint32_t n = p.hdr->n_cams;
     const uint32_t total = p.hdr->total_tiles;
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) s_base[i] = p.cams[i].tile_base;
+    fill_levels(s_lv, p.world);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -497,7 +516,7 @@ __global__ void __launch_bounds__(kThreads, HF_TRACE_MIN_BLOCKS) k_trace_batched
             else hi = mid;
         }
         const CamDev &c = stage_cam(&s_cam[threadIdx.x >> 5], p.cams, lo, lane);
-        trace_tile<SHADOWS, STATS>(p, c, t - s_base[lo], lane);
+        trace_tile<SHADOWS, STATS>(p, s_lv, c, t - s_base[lo], lane);
     }
 }
 
@@ -506,11 +525,14 @@ template <bool SHADOWS, bool STATS>
 __global__ void __launch_bounds__(kThreads, HF_TRACE_MIN_BLOCKS) k_trace_plain(const RenderParams p, uint32_t cam,
                                                           uint32_t n_tiles) {
     __shared__ CamDev s_cam[kThreads / 32];
+    __shared__ LevelDev s_lv[kMaxLevels + 1];
+    fill_levels(s_lv, p.world);
+    __syncthreads();
     const uint32_t t = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
     if (t >= n_tiles) return;
     const int lane = threadIdx.x & 31;
     const CamDev &c = stage_cam(&s_cam[threadIdx.x >> 5], p.cams, cam, lane);
-    trace_tile<SHADOWS, STATS>(p, c, t, lane);
+    trace_tile<SHADOWS, STATS>(p, s_lv, c, t, lane);
 }
 
 template <bool SH, bool ST>
