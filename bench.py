@@ -380,31 +380,53 @@ def run_hf(args):
             pms.append(a.elapsed_time(b))
         plain = n_rays(max_cams) / (float(np.median(pms)) / 1e3)
 
-    # end to end through the public API with host buffers
-    e2e = None
+    # end to end through the public API with host buffers: host camera records
+    # and edit cells in, every output field back in pinned host memory, timed
+    # on the host clock around the whole call.  Path 1 (reported): the kernel
+    # writes the pinned host buffers itself (HF_HOST_OUTPUTS).  Path 2
+    # (context): device buffers, then one copy per output field.
+    e2e = e2e_copy = None
     if not args.no_e2e:
-        host = [{k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in o.items()}
-                for o in outs[:len(max_cams)]]
+        host = hf.alloc_outputs(max_cams, device="pinned", shadows=wl["shadows"])
         cam_bytes = max_cams.nbytes
         out_bytes = sum(v.numel() * v.element_size() for o in host for v in o.values())
-        ems = []
-        for i in range(max(1, min(3, args.steps))):
-            with torch.cuda.stream(stream):
-                flush.fill_(9)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            if wl["edit"]:
-                do_edit()
-            hf.hf_render(ctx, max_cams, outs[:len(max_cams)], opts)
-            with torch.cuda.stream(stream):
-                for o, h in zip(outs, host):
-                    for k in o:
-                        h[k].copy_(o[k], non_blocking=True)
-            stream.synchronize()
-            ems.append(time.perf_counter() - t0)
-        e2e = {"value": n_rays(max_cams) / float(np.median(ems)), "unit": "primary rays/s",
+        if tuned is not None:
+            from paper_2608_17390_gb300.autotune import autotune
+
+            hopts, htable = autotune(ctx, max_cams, host, stream, shadows=wl["shadows"], reps=2,
+                                     mips=(mip_start,), host_outputs=True)
+        else:
+            hopts = hf.hf_render_opts.from_buffer_copy(opts)
+            hopts.flags |= hf.HF_HOST_OUTPUTS
+
+        def e2e_time(via_host):
+            ems = []
+            for i in range(max(1, min(3, args.steps))):
+                with torch.cuda.stream(stream):
+                    flush.fill_(9)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                if wl["edit"]:
+                    do_edit()
+                if via_host:
+                    hf.hf_render(ctx, max_cams, host, hopts)
+                else:
+                    hf.hf_render(ctx, max_cams, outs[:len(max_cams)], opts)
+                    with torch.cuda.stream(stream):
+                        for o, h in zip(outs, host):
+                            for k in o:
+                                h[k].copy_(o[k], non_blocking=True)
+                stream.synchronize()
+                ems.append(time.perf_counter() - t0)
+            return n_rays(max_cams) / float(np.median(ems))
+
+        e2e_copy = e2e_time(False)
+        e2e = {"value": e2e_time(True), "unit": "primary rays/s",
                "h2d_bytes_per_step": int(cam_bytes + (64 * 64 * 4 if wl["edit"] else 0)),
-               "d2h_bytes_per_step": int(out_bytes)}
+               "d2h_bytes_per_step": int(out_bytes),
+               "path": "hf_render with HF_HOST_OUTPUTS: the kernel writes pinned host buffers",
+               "tile": "%dx%d" % (hopts.tile_w or 8, hopts.tile_h or 4),
+               "render_then_copy": e2e_copy}
 
     hf.hf_destroy(ctx)
     if rank != 0:

@@ -68,6 +68,9 @@ extern "C" {
 #define HF_STATS 8u   /* count node and cell fetches (read back with hf_stats) */
 #define HF_NOGRAPH 16u /* launch directly instead of replaying a captured CUDA graph */
 #define HF_NOWAIT 32u /* return HF_E_BUSY instead of waiting for a free render slot */
+#define HF_HOST_OUTPUTS 64u /* the output buffers are pinned HOST memory (cudaHostAlloc or
+                               cudaHostRegister): the kernel writes the results there itself,
+                               over the host link, with no separate copy (hf_render only) */
 
 #define HF_MIP_AUTO 0xFFFFFFFFu
 
@@ -96,9 +99,10 @@ typedef struct {
     uint32_t w, h;
 } hf_camera;
 
-/* Per-camera DEVICE output buffers, each w*h elements in row-major pixel
- * order (py*w + px).  Caller-owned; they must stay allocated until the render
- * has completed on the context's stream.  A NULL member is not written. */
+/* Per-camera output buffers, each w*h elements in row-major pixel order
+ * (py*w + px): DEVICE memory, or pinned HOST memory with HF_HOST_OUTPUTS.
+ * Caller-owned; they must stay allocated until the render has completed on
+ * its stream.  A NULL member is not written. */
 typedef struct {
     uint32_t *hit_cell; /* y*W + x of the hit cell; 0xFFFFFFFF on a miss */
     uint8_t *layer;     /* 0 floor, 1 slab, 255 miss */
@@ -109,12 +113,13 @@ typedef struct {
 } hf_outputs;
 
 typedef struct {
-    uint32_t tile_w, tile_h; /* pixels per warp tile (powers of two, product 32..128);
+    uint32_t tile_w, tile_h; /* pixels per warp tile (powers of two, product 32..256);
                                 0,0 = default 8 x 4 */
     uint32_t mip_start;      /* coarsest pyramid level the traversal uses and starts at;
                                 0 = flat cell-by-cell DDA; HF_MIP_AUTO = library default;
                                 larger values are clamped to the pyramid's top level */
-    uint32_t flags;          /* HF_SHADOWS | HF_PLAIN | HF_SYNC | HF_STATS | HF_NOGRAPH | HF_NOWAIT */
+    uint32_t flags;          /* HF_SHADOWS | HF_PLAIN | HF_SYNC | HF_STATS | HF_NOGRAPH | HF_NOWAIT
+                                | HF_HOST_OUTPUTS */
     uint32_t max_steps;      /* traversal iterations allowed per ray; 0 = default guard */
     int32_t sun[3];          /* direction toward the sun; all zero = (321060, -321060, 262144),
                                 elevation 30 deg, azimuth 135 deg; each |sun_i| < 2^21 */
@@ -154,11 +159,15 @@ int hf_edit(hf_ctx *ctx, uint32_t x0, uint32_t y0, uint32_t w, uint32_t h,
             const uint32_t *cells, size_t row_stride);
 
 /* Render n cameras (HOST array) into outs[0..n-1] (HOST array of structs that
- * hold DEVICE pointers).  Asynchronous on the render stream unless HF_SYNC.
+ * hold DEVICE pointers, or pinned HOST pointers with HF_HOST_OUTPUTS: each
+ * non-NULL one is then checked with cudaPointerGetAttributes and replaced by
+ * its device alias; the results are in host memory once the render's stream
+ * has completed).  Asynchronous on the render stream unless HF_SYNC.
  * opts = NULL uses the defaults.  n = 0 is a no-op.
  * Errors: HF_E_INVALID_ARG (null, n > HF_MAX_CAMERAS, invalid camera or tile
- * shape), HF_E_BUSY (HF_NOWAIT and no free slot), HF_E_CUDA, and with HF_SYNC
- * HF_E_STEP_LIMIT when a ray hit its step guard. */
+ * shape, with HF_HOST_OUTPUTS an output pointer that is neither device memory
+ * nor mapped pinned host memory), HF_E_BUSY (HF_NOWAIT and no free slot),
+ * HF_E_CUDA, and with HF_SYNC HF_E_STEP_LIMIT when a ray hit its step guard. */
 int hf_render(hf_ctx *ctx, const hf_camera *cams, uint32_t n, const hf_outputs *outs,
               const hf_render_opts *opts);
 

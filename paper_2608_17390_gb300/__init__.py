@@ -40,6 +40,7 @@ HF_SYNC = 4
 HF_STATS = 8
 HF_NOGRAPH = 16
 HF_NOWAIT = 32
+HF_HOST_OUTPUTS = 64
 HF_MIP_AUTO = 0xFFFFFFFF
 HF_MAX_DIM = 16384
 HF_MAX_CAMERAS = 4096
@@ -211,7 +212,8 @@ def make_opts(tile_w=0, tile_h=0, mip_start=HF_MIP_AUTO, flags=0, max_steps=0, s
 
 
 def hf_render(ctx, cams, outs, opts=None):
-    """Render camera records into per-camera dicts of device tensors.
+    """Render camera records into per-camera dicts of device tensors (pinned
+    host tensors with HF_HOST_OUTPUTS in opts.flags).
 
     cams: CAMERA_DTYPE array (or records with the same fields); outs: a list
     of dicts keyed by hit_cell, layer, face, depth, rgba, shadow (missing or
@@ -322,7 +324,8 @@ def hf_stats(ctx):
 
 
 def alloc_outputs(cams, device="cuda", shadows=False, fields=OUTPUT_FIELDS):
-    """Allocate one dict of device tensors per camera (torch)."""
+    """Allocate one dict of tensors per camera (torch): on `device`, or in
+    pinned host memory when device is "pinned" (for HF_HOST_OUTPUTS)."""
     import torch
     dt = dict(hit_cell=torch.int32, layer=torch.uint8, face=torch.uint8, depth=torch.float32,
               rgba=torch.int32, shadow=torch.uint8)
@@ -333,6 +336,9 @@ def alloc_outputs(cams, device="cuda", shadows=False, fields=OUTPUT_FIELDS):
         for k in fields:
             if k == "shadow" and not shadows:
                 continue
-            o[k] = torch.empty(n, dtype=dt[k], device=device)
+            if device == "pinned":
+                o[k] = torch.empty(n, dtype=dt[k], pin_memory=True)
+            else:
+                o[k] = torch.empty(n, dtype=dt[k], device=device)
         outs.append(o)
     return outs

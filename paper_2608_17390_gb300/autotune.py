@@ -16,9 +16,13 @@ import threading
 
 import numpy as np
 
-from . import HF_MIP_AUTO, HF_SHADOWS, hf_info, hf_render, hf_sync, make_opts
+from . import HF_HOST_OUTPUTS, HF_MIP_AUTO, HF_SHADOWS, hf_info, hf_render, hf_sync, make_opts
 
 DEFAULT_TILES = ((8, 4), (4, 8), (16, 2), (8, 8), (16, 4), (8, 16))
+# With HF_HOST_OUTPUTS the kernel's stores cross the host link, where a warp
+# store of a short row piece costs nearly as much as a whole line: tiles whose
+# rows are 32 pixels or wider keep those stores long.
+HOST_TILES = ((16, 8), (32, 4), (64, 2), (64, 4), (128, 2), (256, 1))
 DEFAULT_MIPS = (3, 4, 5, 6, 8)
 
 _lock = threading.Lock()
@@ -31,12 +35,12 @@ def resolution_class(cams):
     return int(np.log2(max(1.0, float(np.mean(px)))))
 
 
-def _key(ctx, cams, shadows):
+def _key(ctx, cams, shadows, host_outputs=False):
     import torch
 
     info = hf_info(ctx)
     return (torch.cuda.get_device_name(info["device"]), info["width"], info["height"],
-            resolution_class(cams), bool(shadows))
+            resolution_class(cams), bool(shadows), bool(host_outputs))
 
 
 def _time(ctx, cams, outs, opts, stream, reps):
@@ -54,15 +58,19 @@ def _time(ctx, cams, outs, opts, stream, reps):
     return float(np.median(ts))
 
 
-def autotune(ctx, cams, outs, stream, shadows=False, tiles=DEFAULT_TILES, mips=DEFAULT_MIPS,
-             reps=3, cache_file=None):
+def autotune(ctx, cams, outs, stream, shadows=False, tiles=None, mips=DEFAULT_MIPS,
+             reps=3, cache_file=None, host_outputs=False):
     """Pick (tile_w, tile_h, mip_start) for this batch shape.
 
     ctx must order its work on `stream` (a torch.cuda.Stream); outs are the
-    batch's output buffers (overwritten).  Returns (opts, table) where table
-    lists (tile_w, tile_h, mip, ms) for every candidate timed (empty when the
-    choice came from the cache)."""
-    key = _key(ctx, cams, shadows)
+    batch's output buffers (overwritten; pinned host tensors when
+    host_outputs, which tunes and returns options with HF_HOST_OUTPUTS).
+    tiles defaults to DEFAULT_TILES, or HOST_TILES for host outputs.  Returns
+    (opts, table) where table lists (tile_w, tile_h, mip, ms) for every
+    candidate timed (empty when the choice came from the cache)."""
+    if tiles is None:
+        tiles = HOST_TILES if host_outputs else DEFAULT_TILES
+    key = _key(ctx, cams, shadows, host_outputs)
     with _lock:
         if not _cache and cache_file and os.path.exists(cache_file):
             try:
@@ -71,7 +79,7 @@ def autotune(ctx, cams, outs, stream, shadows=False, tiles=DEFAULT_TILES, mips=D
             except (OSError, ValueError):
                 pass
         hit = _cache.get(key)
-    flags = HF_SHADOWS if shadows else 0
+    flags = (HF_SHADOWS if shadows else 0) | (HF_HOST_OUTPUTS if host_outputs else 0)
     if hit is not None:
         tw, th, mip = hit
         return make_opts(tile_w=tw, tile_h=th, mip_start=mip, flags=flags), []

@@ -548,8 +548,23 @@ struct Batch {
     cudaStream_t stream;
 };
 
+// A pinned host buffer's device alias (device memory passes unchanged);
+// nullptr for memory the GPU cannot address (pageable or unknown).
+static void *device_alias(void *ptr) {
+    if (!ptr) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return ptr;
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) return a.devicePointer;
+    return nullptr;
+}
+
 static int prepare_batch(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_outputs *outs,
-                         uint32_t tw, uint32_t th, bool nowait, void *user_stream, Batch &b) {
+                         uint32_t tw, uint32_t th, bool nowait, void *user_stream, Batch &b,
+                         bool host_outputs = false) {
     const int twl = ilog2_exact(tw), thl = ilog2_exact(th);
     if (twl < 0 || thl < 0 || tw * th < 32 || tw * th > 256 || tw > 256 || th > 256)
         return HF_E_INVALID_ARG;
@@ -597,6 +612,18 @@ static int prepare_batch(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_
         v.depth = outs[i].depth;
         v.rgba = outs[i].rgba;
         v.shadow = outs[i].shadow;
+        if (host_outputs) {
+            const hf_outputs &u = outs[i];
+            v.hit_cell = static_cast<uint32_t *>(device_alias(u.hit_cell));
+            v.layer = static_cast<uint8_t *>(device_alias(u.layer));
+            v.face = static_cast<uint8_t *>(device_alias(u.face));
+            v.depth = static_cast<float *>(device_alias(u.depth));
+            v.rgba = static_cast<uint32_t *>(device_alias(u.rgba));
+            v.shadow = static_cast<uint8_t *>(device_alias(u.shadow));
+            if ((u.hit_cell && !v.hit_cell) || (u.layer && !v.layer) || (u.face && !v.face) ||
+                (u.depth && !v.depth) || (u.rgba && !v.rgba) || (u.shadow && !v.shadow))
+                return HF_E_INVALID_ARG;  // the slot was not yet marked in flight
+        }
     }
     std::memset(&b.p, 0, sizeof(b.p));
     b.p.world = c->wd;
@@ -644,7 +671,8 @@ int hf_render(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_outputs *ou
     const uint32_t steps = o.max_steps ? o.max_steps : (uint32_t)(guard > 0x7FFFFFFF ? 0x7FFFFFFF : guard);
     if (steps > 0x7FFFFFFFu) return HF_E_INVALID_ARG;
     Batch b;
-    int rc = prepare_batch(c, cams, n, outs, tw, th, (o.flags & HF_NOWAIT) != 0, o.cuda_stream, b);
+    int rc = prepare_batch(c, cams, n, outs, tw, th, (o.flags & HF_NOWAIT) != 0, o.cuda_stream, b,
+                           (o.flags & HF_HOST_OUTPUTS) != 0);
     if (rc != HF_OK) return rc;
     Slot &s = c->slots[b.slot];
     hf::RenderParams &p = b.p;

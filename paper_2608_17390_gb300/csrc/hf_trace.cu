@@ -218,6 +218,7 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const LevelDev *lvt
     // ray never leaves through that axis.
     const int32_t gx = r.dx < 0 ? -1 : 1, gy = r.dy < 0 ? -1 : 1;  // step per exit
     const int32_t px = r.dx < 0 ? 0 : 1, py = r.dy < 0 ? 0 : 1;    // exit side offset
+    const int32_t qx = px ^ 1, qy = py ^ 1;
     const int32_t kx = -gx * r.ox, ky = -gy * r.oy;
     const uint8_t face_x = r.dx < 0 ? kFacePX : kFaceNX;  // entry face of an x crossing
     const uint8_t face_y = r.dy < 0 ? kFacePY : kFaceNY;
@@ -290,14 +291,13 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const LevelDev *lvt
         tin_num = tout_num;
         tin_den = tout_den;
         if ((uint32_t)nx >= lv.stride || (uint32_t)ny >= lv.rows) return;
-        if (level < mip_start) {  // ascend when the crossed boundary is a parent boundary
-            const int32_t bnd = cmp <= 0 ? bx : by;
-            if ((bnd & ((2 << level) - 1)) == 0) {
-                ++level;
-                nx >>= 1;
-                ny >>= 1;
-
-            }
+        // ascend when the crossed boundary is a parent boundary: the new index
+        // on the crossed axis is then even (odd for a negative direction)
+        const int32_t crossed = cmp <= 0 ? (nx ^ qx) : (ny ^ qy);
+        if (level < mip_start && (crossed & 1) == 0) {
+            ++level;
+            nx >>= 1;
+            ny >>= 1;
         }
     }
     h.face = kFaceError;

@@ -47,6 +47,20 @@ def test_binding_names_match_the_abi(hf):
         assert callable(getattr(hf, n)), n
 
 
+def test_header_constants_match_the_binding(hf):
+    """Every numeric #define HF_* in include/ has the same value in the binding."""
+    seen = 0
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        for name, val in re.findall(r"#define\s+(HF_\w+)\s+\(?(-?(?:0x[0-9A-Fa-f]+|\d+))u?\)?", src):
+            if hasattr(hf, name):
+                assert getattr(hf, name) == int(val, 0), name
+                seen += 1
+    assert seen >= 15
+
+
 def test_strerror(hf):
     for code in range(0, -7, -1):
         assert hf.hf_strerror(code) and hf.hf_strerror(code) != "unknown error"

@@ -63,5 +63,16 @@ def test_every_candidate_gives_identical_buffers(hf, tmp_path):
         opts2, table2 = autotune(ctx, cams, outs, stream, shadows=True, cache_file=cache)
         assert table2 == [] and (opts2.tile_w, opts2.tile_h, opts2.mip_start) == (
             opts.tile_w, opts.tile_h, opts.mip_start)
+        # host outputs are tuned separately, over the wide tiles, and the tuned
+        # render into pinned host buffers gives the same result
+        host = hf.alloc_outputs(cams, device="pinned", shadows=True)
+        hopts, htable = autotune(ctx, cams, host, stream, shadows=True, reps=1, mips=(5,),
+                                 host_outputs=True)
+        assert len(htable) == 6 and hopts.flags & hf.HF_HOST_OUTPUTS
+        hf.hf_render(ctx, cams, host, hopts)
+        hf.hf_sync(ctx)
+        for i in range(len(cams)):
+            for k in ref[i]:
+                assert np.array_equal(ref[i][k], host[i][k].numpy()), ("host", i, k)
     finally:
         hf.hf_destroy(ctx)

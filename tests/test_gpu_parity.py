@@ -525,3 +525,28 @@ def test_nowait_admission_reports_busy(hf):
             compare({k: v[pix] for k, v in g[i].items()}, o, what="after busy cam %d" % i)
     finally:
         hf.hf_destroy(ctx)
+
+
+def test_host_outputs_equal_device_outputs(hf, c1):
+    """HF_HOST_OUTPUTS: the kernel writes pinned host buffers itself; the
+    results equal the device-buffer render bit for bit, and pageable host
+    memory is rejected before anything runs."""
+    import torch
+
+    cells, cams = c1["cells"], c1["cams"]
+    ctx = _ctx(hf, cells)
+    try:
+        dev = gpu_render(hf, ctx, cams, shadows=True, opts=hf.make_opts(flags=hf.HF_SHADOWS))
+        for extra in (0, hf.HF_NOGRAPH):
+            host = hf.alloc_outputs(cams, device="pinned", shadows=True)
+            hf.hf_render(ctx, cams, host,
+                         hf.make_opts(flags=hf.HF_SHADOWS | hf.HF_HOST_OUTPUTS | hf.HF_SYNC | extra))
+            for k, t in host[0].items():
+                assert (t.numpy() == dev[0][k].view(t.numpy().dtype)).all(), k
+        pageable = [{k: torch.empty(v.shape, dtype=v.dtype) for k, v in o.items()} for o in host]
+        with pytest.raises(hf.HFError):
+            hf.hf_render(ctx, cams, pageable,
+                         hf.make_opts(flags=hf.HF_SHADOWS | hf.HF_HOST_OUTPUTS))
+        hf.hf_sync(ctx)
+    finally:
+        hf.hf_destroy(ctx)
