@@ -25,6 +25,7 @@ from .terrain import (
     grid_hash,
     crater_edit,
 )
+from .pairs import pairify, encode_pairs
 from .cameras import (
     CAMERA_DTYPE,
     pose_to_camera,
