@@ -151,6 +151,14 @@ def workload(name, rank=0, scale=1, frames_per_step=100):
                          "1920x1080 fly-through; one step = %d frames in one batch" % frames_per_step,
                     cells=cells, cams=synth.config_c4_frames(cells, 1000), shadows=False,
                     edit=False, frames_per_step=frames_per_step)
+    if name == "c4pair":
+        cells = synth.pairify(synth.config_c4()["cells"] & np.uint32(0x07FFFFFF))
+        return dict(name="C4 large world in paired 2-byte texels (64 MiB of cells): 2048x16384 "
+                         "grid (seed 4, 30%% slabs, slab pairs sharing one column), 1000-frame "
+                         "1920x1080 fly-through; one step = %d frames in one batch" % frames_per_step,
+                    cells=cells, texels=synth.encode_pairs(cells),
+                    cams=synth.config_c4_frames(cells, 1000), shadows=False, edit=False,
+                    frames_per_step=frames_per_step)
     raise SystemExit("unknown workload " + name)
 
 
@@ -260,7 +268,10 @@ def run_hf(args):
     cams_all = wl["cams"]
     fps = wl.get("frames_per_step")
     stream = torch.cuda.Stream()
-    ctx = hf.hf_create(cells, stream=stream.cuda_stream)
+    if "texels" in wl:
+        ctx = hf.hf_create_pairs(wl["texels"], stream=stream.cuda_stream)
+    else:
+        ctx = hf.hf_create(cells, stream=stream.cuda_stream)
     info = hf.hf_info(ctx)
     flags = hf.HF_SHADOWS if wl["shadows"] else 0
 
@@ -288,6 +299,12 @@ def run_hf(args):
     def do_edit():
         cx, cy = int(rng.integers(0, W)), int(rng.integers(0, H))
         x0, y0, blk = synth.crater_edit(cells, cx, cy)
+        if "texels" in wl:  # a paired-texel world is edited in whole, representable pairs
+            h, w = blk.shape
+            xa, xb = x0 & ~1, (x0 + w + 1) & ~1
+            full = cells[y0:y0 + h, xa:xb].copy()
+            full[:, x0 - xa:x0 - xa + w] = blk
+            x0, blk = xa, synth.pairify(full)
         hf.hf_edit(ctx, x0, y0, blk)
         cells[y0:y0 + blk.shape[0], x0:x0 + blk.shape[1]] = blk
 
@@ -649,7 +666,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hf", choices=["hf", "reference"])
     ap.add_argument("--workload", default="c3",
-                    choices=["c1", "c2", "c3", "c4", "c5", "protocol"])
+                    choices=["c1", "c2", "c3", "c4", "c4pair", "c5", "protocol"])
     ap.add_argument("--serve-requests", type=int, default=2200)
     ap.add_argument("--frames-per-step", type=int, default=100,
                     help="large-world fly-through frames rendered per step (one batch)")

@@ -77,6 +77,10 @@ extern "C" {
 #define HF_MAX_DIM 16384u     /* largest grid width/height and image width/height */
 #define HF_MAX_CAMERAS 4096u  /* largest batch in one hf_render call */
 
+/* hf_info_t.cell_format: how the device stores the cells (level 0) */
+#define HF_CELLS_WORD32 0u /* one 4-byte word per cell (hf_create) */
+#define HF_CELLS_PAIR16 1u /* one 2-byte texel per cell, paired (hf_create_pairs) */
+
 /* --------------------------------------------------------------- types */
 typedef struct hf_ctx hf_ctx; /* opaque: owns the device grid, pyramid and scratch */
 
@@ -87,6 +91,26 @@ typedef struct {
     void *cuda_stream;      /* cudaStream_t all work of this context is ordered on;
                                NULL: the library creates (and destroys) its own */
 } hf_desc;
+
+/* A world in the paired-texel encoding of the paper's data section (Section 2,
+ * The Data: a double-level region stores, per texel PAIR, the floor top in the
+ * even texel, the slab top in the odd texel, and the cave ceiling as delta bits
+ * in both).  The paper gives no bit layout; this library's is:
+ *   texel = uint16: low byte altitude v, high byte meta m;
+ *   m bit 7 = the pair (x even, x + 1) is double-level (equal on both texels),
+ *   m bits 6..3 = a delta nibble, m bits 2..0 = material (0..7).
+ *   Single-level pair: each texel is a cell with h0 = v, no slab; both nibbles 0.
+ *   Double-level pair: both cells have h0 = v(even), h2 = v(odd),
+ *   h1 = h2 - (16 * nibble(even) + nibble(odd)), needing h0 < h1 <= h2, and the
+ *   material of their own texel.
+ * The device keeps 2 bytes per cell (half of hf_create's) and decodes in the
+ * kernels; every result equals that of hf_create on the decoded cells. */
+typedef struct {
+    uint32_t width, height;  /* grid size in cells; width even, 2..HF_MAX_DIM */
+    const uint16_t *texels;  /* HOST pointer to height rows of row_stride texels */
+    size_t row_stride;       /* texels per row; 0 means width */
+    void *cuda_stream;       /* as in hf_desc */
+} hf_pair_desc;
 
 /* Integer camera.  Pixel (px, py), py = 0 at the top row, looks along
  *   d = fwd + (2 px + 1 - w) right + (h - 1 - 2 py) up.
@@ -134,6 +158,8 @@ typedef struct {
     uint64_t scratch_bytes;         /* device bytes of per-render scratch (camera tables) */
     int32_t device;                 /* CUDA device ordinal */
     int32_t sm_count;
+    uint32_t cell_format;           /* HF_CELLS_WORD32 or HF_CELLS_PAIR16 */
+    uint32_t reserved;
 } hf_info_t;
 
 /* ------------------------------------------------------------ functions */
@@ -145,6 +171,11 @@ typedef struct {
  * Errors: HF_E_INVALID_ARG (null, bad size, invalid cell), HF_E_OOM, HF_E_CUDA. */
 int hf_create(const hf_desc *desc, hf_ctx **out);
 
+/* hf_create for a paired-texel world (hf_pair_desc).  The caller may free
+ * desc->texels when this returns.  Errors: HF_E_INVALID_ARG (null, bad or odd
+ * width, a pair that breaks the encoding's rules), HF_E_OOM, HF_E_CUDA. */
+int hf_create_pairs(const hf_pair_desc *desc, hf_ctx **out);
+
 /* Overwrite the cells of rectangle [x0, x0+w) x [y0, y0+h) with `cells` (HOST
  * pointer, h rows of row_stride cells; 0 = w) and repair the pyramid nodes that
  * cover it, level by level (the incremental rebuild of affected cells and their
@@ -153,7 +184,12 @@ int hf_create(const hf_desc *desc, hf_ctx **out);
  * stream after every render issued before it (renders issued on other streams
  * included) and before every render issued after it: those renders see it,
  * earlier ones do not (the first-frame visibility of Section 4.4).
- * w = 0 or h = 0 is a no-op.  Errors: HF_E_INVALID_ARG (null, invalid cell),
+ * For a paired-texel world (hf_create_pairs) the cells are still cell words:
+ * x0 and w must be even, and each pair must be representable (no slab in
+ * either cell, or the same slab column in both, materials 0..7); the library
+ * encodes them.  w = 0 or h = 0 is a no-op.
+ * Errors: HF_E_INVALID_ARG (null, invalid or unrepresentable cell, odd x0 or w
+ * in a paired-texel world),
  * HF_E_OUT_OF_BOUNDS (rectangle outside the grid), HF_E_OOM, HF_E_CUDA. */
 int hf_edit(hf_ctx *ctx, uint32_t x0, uint32_t y0, uint32_t w, uint32_t h,
             const uint32_t *cells, size_t row_stride);
@@ -255,13 +291,20 @@ int hf_validate_camera(uint32_t grid_w, uint32_t grid_h, const hf_camera *cam);
  * Returns HF_OK or HF_E_INVALID_ARG; *bad_index (may be NULL) gets the first bad word. */
 int hf_validate_cells(const uint32_t *cells, size_t n, size_t *bad_index);
 
+/* Host check of a width x height grid of paired texels (hf_pair_desc rules;
+ * row_stride 0 = width).  Returns HF_OK or HF_E_INVALID_ARG; *bad_index (may
+ * be NULL) gets y * width + x of the even texel of the first bad pair. */
+int hf_validate_pairs(const uint16_t *texels, uint32_t width, uint32_t height, size_t row_stride,
+                      size_t *bad_index);
+
 /* Static text for a code (never NULL). */
 const char *hf_strerror(int code);
 
 /* Sizes and device of a context.  Errors: HF_E_INVALID_ARG. */
 int hf_info(const hf_ctx *ctx, hf_info_t *out);
 
-/* Copy cells of a rectangle back to HOST memory (synchronous).
+/* Copy cells of a rectangle back to HOST memory as cell words (synchronous;
+ * a paired-texel world is decoded).
  * Errors: HF_E_INVALID_ARG, HF_E_OUT_OF_BOUNDS, HF_E_CUDA. */
 int hf_read_cells(hf_ctx *ctx, uint32_t x0, uint32_t y0, uint32_t w, uint32_t h,
                   uint32_t *out, size_t row_stride);

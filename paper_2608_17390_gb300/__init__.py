@@ -45,6 +45,8 @@ HF_MIP_AUTO = 0xFFFFFFFF
 HF_MAX_DIM = 16384
 HF_MAX_CAMERAS = 4096
 HF_NOALLOC_MAX_CAMERAS = 256
+HF_CELLS_WORD32 = 0
+HF_CELLS_PAIR16 = 1
 
 
 class HFError(RuntimeError):
@@ -56,6 +58,12 @@ class HFError(RuntimeError):
 class hf_desc(ctypes.Structure):
     _fields_ = [("width", ctypes.c_uint32), ("height", ctypes.c_uint32),
                 ("cells", ctypes.c_void_p), ("row_stride", ctypes.c_size_t),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class hf_pair_desc(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_uint32), ("height", ctypes.c_uint32),
+                ("texels", ctypes.c_void_p), ("row_stride", ctypes.c_size_t),
                 ("cuda_stream", ctypes.c_void_p)]
 
 
@@ -90,7 +98,8 @@ class hf_info_t(ctypes.Structure):
                 ("levels", ctypes.c_uint32), ("render_slots", ctypes.c_uint32),
                 ("cell_bytes", ctypes.c_uint64), ("pyramid_bytes", ctypes.c_uint64),
                 ("scratch_bytes", ctypes.c_uint64), ("device", ctypes.c_int32),
-                ("sm_count", ctypes.c_int32)]
+                ("sm_count", ctypes.c_int32), ("cell_format", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
 
 # numpy view of hf_camera (same layout as the C struct)
@@ -105,6 +114,9 @@ _P = ctypes.c_void_p
 _U32 = ctypes.c_uint32
 _SIGS = {
     "hf_create": ([ctypes.POINTER(hf_desc), ctypes.POINTER(_P)], ctypes.c_int),
+    "hf_create_pairs": ([ctypes.POINTER(hf_pair_desc), ctypes.POINTER(_P)], ctypes.c_int),
+    "hf_validate_pairs": ([_P, _U32, _U32, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)],
+                          ctypes.c_int),
     "hf_edit": ([_P, _U32, _U32, _U32, _U32, _P, ctypes.c_size_t], ctypes.c_int),
     "hf_render": ([_P, _P, _U32, _P, ctypes.POINTER(hf_render_opts)], ctypes.c_int),
     "hf_render_noalloc": ([_P, _P, _U32, _P, ctypes.POINTER(hf_render_opts)], ctypes.c_int),
@@ -176,6 +188,30 @@ def hf_create(cells, stream=None):
     h = _P()
     _check(lib.hf_create(ctypes.byref(d), ctypes.byref(h)), "hf_create")
     return h.value
+
+
+def hf_create_pairs(texels, stream=None):
+    """Create a context from a uint16 [H, W] host array of paired texels (W
+    even; the encoding is described in include/hf.h at hf_pair_desc)."""
+    t = np.ascontiguousarray(texels, dtype=np.uint16)
+    if t.ndim != 2:
+        raise ValueError("texels must be a 2-D array")
+    H, W = t.shape
+    d = hf_pair_desc(W, H, t.ctypes.data, W, stream if stream is not None else _current_stream())
+    h = _P()
+    _check(lib.hf_create_pairs(ctypes.byref(d), ctypes.byref(h)), "hf_create_pairs")
+    return h.value
+
+
+def hf_validate_pairs(texels):
+    """Returns (code, index of the first bad pair's even texel or None)."""
+    t = np.ascontiguousarray(texels, dtype=np.uint16)
+    if t.ndim != 2:
+        raise ValueError("texels must be a 2-D array")
+    H, W = t.shape
+    bad = ctypes.c_size_t(0)
+    rc = lib.hf_validate_pairs(t.ctypes.data if t.size else None, W, H, W, ctypes.byref(bad))
+    return rc, (bad.value if rc != HF_OK else None)
 
 
 def hf_edit(ctx, x0, y0, block):

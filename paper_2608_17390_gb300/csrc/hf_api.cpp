@@ -66,6 +66,7 @@ struct hf_ctx {
     unsigned long long *d_stats = nullptr;
     int occ[2][2] = {{0, 0}, {0, 0}};
     int occ_march = 0;
+    bool pair = false;  // level 0 holds paired 2-byte texels (hf_create_pairs)
 };
 
 #define CK(call)                                   \
@@ -82,6 +83,48 @@ bool cell_ok(uint32_t c) {
     const uint32_t h0 = c & 0xFF, h1 = (c >> 8) & 0xFF, h2 = (c >> 16) & 0xFF;
     if (h1 > h0) return h2 >= h1;
     return h1 == 0 && h2 == 0;
+}
+
+// One pair of 2-byte texels (altitude | meta << 8): the pair encoding's rules
+// (include/hf.h, hf_create_pairs).
+bool pair_ok(uint16_t e, uint16_t o) {
+    const uint32_t ve = e & 0xFF, me = e >> 8, vo = o & 0xFF, mo = o >> 8;
+    if ((me >> 7) != (mo >> 7)) return false;
+    const uint32_t ne = (me >> 3) & 15, no = (mo >> 3) & 15;
+    if (!(me >> 7)) return ne == 0 && no == 0;
+    const int32_t mid = (int32_t)vo - (int32_t)(16 * ne + no);
+    return (int32_t)ve < mid && mid <= (int32_t)vo;
+}
+
+int check_pair_rows(const uint16_t *t, uint32_t w, uint32_t h, size_t stride, size_t *bad) {
+    if (w % 2) return HF_E_INVALID_ARG;
+    for (uint32_t y = 0; y < h; ++y)
+        for (uint32_t x = 0; x < w; x += 2)
+            if (!pair_ok(t[(size_t)y * stride + x], t[(size_t)y * stride + x + 1])) {
+                if (bad) *bad = (size_t)y * w + x;
+                return HF_E_INVALID_ARG;
+            }
+    return HF_OK;
+}
+
+// Two valid cell words as one pair of texels; false when the pair encoding
+// cannot hold them (one slab without the other, or different slab columns).
+bool encode_pair(uint32_t ce, uint32_t co, uint16_t *te, uint16_t *to) {
+    const uint32_t e0 = ce & 0xFF, e1 = (ce >> 8) & 0xFF, e2 = (ce >> 16) & 0xFF, em = (ce >> 24) & 7;
+    const uint32_t o0 = co & 0xFF, o1 = (co >> 8) & 0xFF, o2 = (co >> 16) & 0xFF, om = (co >> 24) & 7;
+    if ((ce >> 27) || (co >> 27)) return false;  // materials above 7 have no room
+    const bool se = e1 > e0, so = o1 > o0;
+    if (se != so) return false;
+    if (!se) {
+        *te = (uint16_t)(e0 | (em << 8));
+        *to = (uint16_t)(o0 | (om << 8));
+        return true;
+    }
+    if (e0 != o0 || e1 != o1 || e2 != o2) return false;
+    const uint32_t delta = e2 - e1;  // 0..254
+    *te = (uint16_t)(e0 | ((0x80 | ((delta >> 4) << 3) | em) << 8));
+    *to = (uint16_t)(e2 | ((0x80 | ((delta & 15) << 3) | om) << 8));
+    return true;
 }
 
 int check_rows(const uint32_t *cells, uint32_t w, uint32_t h, size_t stride) {
@@ -181,6 +224,14 @@ int hf_validate_cells(const uint32_t *cells, size_t n, size_t *bad_index) {
     return HF_OK;
 }
 
+int hf_validate_pairs(const uint16_t *texels, uint32_t width, uint32_t height, size_t row_stride,
+                      size_t *bad_index) {
+    if ((!texels && width && height) || width % 2) return HF_E_INVALID_ARG;
+    const size_t stride = row_stride ? row_stride : width;
+    if (stride < width) return HF_E_INVALID_ARG;
+    return check_pair_rows(texels, width, height, stride, bad_index);
+}
+
 int hf_validate_camera(uint32_t W, uint32_t H, const hf_camera *c) {
     if (!c || W == 0 || H == 0 || W > HF_MAX_DIM || H > HF_MAX_DIM) return HF_E_INVALID_ARG;
     if (c->w == 0 || c->h == 0 || c->w > HF_MAX_DIM || c->h > HF_MAX_DIM) return HF_E_INVALID_ARG;
@@ -254,7 +305,9 @@ int hf_destroy(hf_ctx *c) {
     return rc;
 }
 
-static int create_impl(const hf_desc *d, hf_ctx *c) {
+// d->cells holds cell words, or (texels != nullptr) paired 2-byte texels.
+static int create_impl(const hf_desc *d, hf_ctx *c, const uint16_t *texels = nullptr) {
+    c->pair = texels != nullptr;
     CK(cudaGetDevice(&c->device));
     CK(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
     c->W = d->width;
@@ -273,22 +326,29 @@ static int create_impl(const hf_desc *d, hf_ctx *c) {
         c->wd.off[k] = (uint32_t)off;
         c->wd.stride[k] = wk;
         c->wd.rows[k] = hk;
-        off += ((size_t)wk * hk + 63) & ~(size_t)63;
+        const size_t words = (k == 0 && c->pair) ? (size_t)wk / 2 * hk : (size_t)wk * hk;
+        off += (words + 63) & ~(size_t)63;
     }
     c->world_words = off;
     c->wd.W = (int32_t)c->W;
     c->wd.H = (int32_t)c->H;
     c->wd.L = (int32_t)c->L;
+    c->wd.pair = c->pair ? 1 : 0;
     if (cudaMalloc(&c->d_world, off * sizeof(uint32_t)) != cudaSuccess) {
         (void)cudaGetLastError();
         return HF_E_OOM;
     }
     c->wd.base = c->d_world;
     const size_t stride = d->row_stride ? d->row_stride : d->width;
-    CK(cudaMemcpy2DAsync(c->d_world, (size_t)c->W * 4, d->cells, stride * 4, (size_t)c->W * 4,
-                         c->H, cudaMemcpyHostToDevice, c->stream));
-    // level 0 is kept in node form (hf::cell_encode)
-    if (hf::cells_encode(c->d_world, c->W * c->H, c->stream)) return HF_E_CUDA;
+    if (c->pair) {  // texels are stored as given
+        CK(cudaMemcpy2DAsync(c->d_world, (size_t)c->W * 2, texels, stride * 2, (size_t)c->W * 2,
+                             c->H, cudaMemcpyHostToDevice, c->stream));
+    } else {
+        CK(cudaMemcpy2DAsync(c->d_world, (size_t)c->W * 4, d->cells, stride * 4,
+                             (size_t)c->W * 4, c->H, cudaMemcpyHostToDevice, c->stream));
+        // level 0 is kept in node form (hf::cell_encode)
+        if (hf::cells_encode(c->d_world, c->W * c->H, c->stream)) return HF_E_CUDA;
+    }
     if (hf::pyramid_build(c->d_world, c->wd, c->stream)) return HF_E_CUDA;
     if (cudaMalloc(&c->d_status, sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc(&c->d_stats, 5 * sizeof(unsigned long long)) != cudaSuccess ||
@@ -304,7 +364,8 @@ static int create_impl(const hf_desc *d, hf_ctx *c) {
     for (auto &s : c->slots) CK(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
     for (int sh = 0; sh < 2; ++sh)
         for (int st = 0; st < 2; ++st)
-            if (hf::trace_batched_occupancy(sh, st, &c->occ[sh][st]) || c->occ[sh][st] < 1)
+            if (hf::trace_batched_occupancy(sh, st, c->pair, &c->occ[sh][st]) ||
+                c->occ[sh][st] < 1)
                 return HF_E_CUDA;
     if (hf::march_occupancy(&c->occ_march) || c->occ_march < 1) return HF_E_CUDA;
     CK(cudaStreamSynchronize(c->stream));
@@ -331,13 +392,40 @@ int hf_create(const hf_desc *d, hf_ctx **out) {
     return HF_OK;
 }
 
+int hf_create_pairs(const hf_pair_desc *d, hf_ctx **out) {
+    if (!out) return HF_E_INVALID_ARG;
+    *out = nullptr;
+    if (!d || !d->texels || d->width == 0 || d->height == 0 || d->width > HF_MAX_DIM ||
+        d->height > HF_MAX_DIM || d->width % 2)
+        return HF_E_INVALID_ARG;
+    const size_t stride = d->row_stride ? d->row_stride : d->width;
+    if (stride < d->width) return HF_E_INVALID_ARG;
+    if (check_pair_rows(d->texels, d->width, d->height, stride, nullptr) != HF_OK)
+        return HF_E_INVALID_ARG;
+    hf_ctx *c = new (std::nothrow) hf_ctx();
+    if (!c) return HF_E_OOM;
+    hf_desc cd{};
+    cd.width = d->width;
+    cd.height = d->height;
+    cd.row_stride = d->row_stride;
+    cd.cuda_stream = d->cuda_stream;
+    const int rc = create_impl(&cd, c, d->texels);
+    if (rc != HF_OK) {
+        hf_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return HF_OK;
+}
+
 int hf_info(const hf_ctx *c, hf_info_t *out) {
     if (!c || !out) return HF_E_INVALID_ARG;
     out->width = c->W;
     out->height = c->H;
     out->levels = c->L;
     out->render_slots = kSlots;
-    out->cell_bytes = (uint64_t)c->W * c->H * 4;
+    out->cell_bytes = (uint64_t)c->W * c->H * (c->pair ? 2 : 4);
+    out->cell_format = c->pair ? HF_CELLS_PAIR16 : HF_CELLS_WORD32;
     out->pyramid_bytes = (uint64_t)(c->world_words - c->wd.off[c->L > 0 ? 1 : 0]) * 4;
     if (c->L == 0) out->pyramid_bytes = 0;
     uint64_t sb = 0;
@@ -357,8 +445,9 @@ int hf_edit(hf_ctx *c, uint32_t x0, uint32_t y0, uint32_t w, uint32_t h, const u
     const size_t stride = row_stride ? row_stride : w;
     if (stride < w) return HF_E_INVALID_ARG;
     if (check_rows(cells, w, h, stride) != HF_OK) return HF_E_INVALID_ARG;
+    if (c->pair && (x0 % 2 || w % 2)) return HF_E_INVALID_ARG;
     CK(cudaSetDevice(c->device));
-    const size_t need = (size_t)w * h * sizeof(uint32_t);
+    const size_t need = (size_t)w * h * (c->pair ? 2 : 4);
     if (c->edit_pending) {
         CK(cudaEventSynchronize(c->edit_copy_done));
         c->edit_pending = false;
@@ -374,16 +463,28 @@ int hf_edit(hf_ctx *c, uint32_t x0, uint32_t y0, uint32_t w, uint32_t h, const u
         }
         c->edit_cap = cap;
     }
-    for (uint32_t y = 0; y < h; ++y) {  // staged in node form (hf::cell_encode)
-        const uint32_t *src = cells + (size_t)y * stride;
-        uint32_t *dst = c->h_edit + (size_t)y * w;
-        for (uint32_t x = 0; x < w; ++x) dst[x] = hf::cell_encode(src[x]);
+    if (c->pair) {  // staged as paired texels
+        uint16_t *t = reinterpret_cast<uint16_t *>(c->h_edit);
+        for (uint32_t y = 0; y < h; ++y) {
+            const uint32_t *src = cells + (size_t)y * stride;
+            for (uint32_t x = 0; x < w; x += 2)
+                if (!encode_pair(src[x], src[x + 1], t + (size_t)y * w + x, t + (size_t)y * w + x + 1))
+                    return HF_E_INVALID_ARG;
+        }
+    } else {
+        for (uint32_t y = 0; y < h; ++y) {  // staged in node form (hf::cell_encode)
+            const uint32_t *src = cells + (size_t)y * stride;
+            uint32_t *dst = c->h_edit + (size_t)y * w;
+            for (uint32_t x = 0; x < w; ++x) dst[x] = hf::cell_encode(src[x]);
+        }
     }
     // no in-flight render may observe the edit
     for (auto &s : c->slots)
         if (s.pending) CK(cudaStreamWaitEvent(c->stream, s.done, 0));
-    CK(cudaMemcpy2DAsync(c->d_world + (size_t)y0 * c->W + x0, (size_t)c->W * 4, c->h_edit,
-                         (size_t)w * 4, (size_t)w * 4, h, cudaMemcpyHostToDevice, c->stream));
+    const size_t cb = c->pair ? 2 : 4;  // bytes per cell at level 0
+    CK(cudaMemcpy2DAsync(reinterpret_cast<char *>(c->d_world) + ((size_t)y0 * c->W + x0) * cb,
+                         (size_t)c->W * cb, c->h_edit, (size_t)w * cb, (size_t)w * cb, h,
+                         cudaMemcpyHostToDevice, c->stream));
     CK(cudaEventRecord(c->edit_copy_done, c->stream));
     c->edit_pending = true;
     if (hf::pyramid_repair(c->d_world, c->wd, (int32_t)x0, (int32_t)y0, (int32_t)(x0 + w),
@@ -419,6 +520,22 @@ int hf_read_cells(hf_ctx *c, uint32_t x0, uint32_t y0, uint32_t w, uint32_t h, u
     const size_t stride = row_stride ? row_stride : w;
     if (stride < w) return HF_E_INVALID_ARG;
     CK(cudaSetDevice(c->device));
+    if (c->pair) {  // the whole pairs that cover the columns, decoded here
+        const uint32_t xa = x0 & ~1u, xb = (x0 + w + 1) & ~1u;
+        std::vector<uint32_t> pw((size_t)(xb - xa) / 2 * h);
+        CK(cudaMemcpy2DAsync(pw.data(), (size_t)(xb - xa) * 2,
+                             reinterpret_cast<const char *>(c->d_world) + ((size_t)y0 * c->W + xa) * 2,
+                             (size_t)c->W * 2, (size_t)(xb - xa) * 2, h, cudaMemcpyDeviceToHost,
+                             c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (uint32_t y = 0; y < h; ++y)
+            for (uint32_t x = 0; x < w; ++x) {
+                const uint32_t cx = x0 + x;
+                out[(size_t)y * stride + x] = hf::cell_decode(
+                    hf::pair_node(pw[(size_t)y * ((xb - xa) / 2) + (cx - xa) / 2], cx & 1));
+            }
+        return HF_OK;
+    }
     CK(cudaMemcpy2DAsync(out, stride * 4, c->d_world + (size_t)y0 * c->W + x0, (size_t)c->W * 4,
                          (size_t)w * 4, h, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -517,7 +634,7 @@ static int launch_graph(hf_ctx *c, Slot &s, const GraphKey &key, const hf::Rende
         hf::RenderParams pc = p;
         void *args[] = {&pc};
         cudaKernelNodeParams kp{};
-        kp.func = const_cast<void *>(hf::trace_batched_fn(shadows, stats));
+        kp.func = const_cast<void *>(hf::trace_batched_fn(shadows, stats, c->pair));
         kp.gridDim = dim3((unsigned)(c->sm_count * c->occ[shadows][stats]));
         kp.blockDim = dim3(hf::kThreads);
         kp.sharedMemBytes = 0;

@@ -2,7 +2,8 @@
 //
 // Memory layout in HBM (one allocation per context, 256-byte aligned levels):
 //   level 0   : the cells, W x H uint32 words, row-major y*W + x, each in node
-//               form with its material (cell_encode below)
+//               form with its material (cell_encode below); or, for a world
+//               created from paired texels, W x H uint16 texels (pair_node)
 //   level k>=1: ceil(W/2^k) x ceil(H/2^k) node words, row-major,
 //               byte0 max h0, byte1 min (slab ? h1 : 255), byte2 max (slab ? h2 : h0)
 // Per-render scratch (one block per render slot):
@@ -32,6 +33,24 @@ __host__ __device__ inline uint32_t cell_decode(uint32_t n) {
     return b2 > b0 ? n : (n & 0xFF0000FFu);
 }
 
+// The node-form word (with material) of cell `odd` (0 even, 1 odd) of a pair
+// of 2-byte texels loaded as one little-endian 32-bit word: altitude and meta
+// byte of the even texel, then of the odd one.  Meta bit 7: the pair is
+// double-level; bits 6..3: a delta nibble; bits 2..0: material.  A
+// double-level pair is one column for both cells, floor top = even altitude,
+// slab top = odd altitude, slab underside = slab top - (16 * even nibble +
+// odd nibble) (the data section's pair encoding, with this bit layout).
+__host__ __device__ inline uint32_t pair_node(uint32_t pw, uint32_t odd) {
+    const uint32_t ve = pw & 0xFF, me = (pw >> 8) & 0xFF, vo = (pw >> 16) & 0xFF, mo = pw >> 24;
+    const uint32_t mat = (odd ? mo : me) & 7;
+    if (me & 0x80) {
+        const uint32_t mid = vo - (((me << 1) & 0xF0) | ((mo >> 3) & 0x0F));
+        return ve | (mid << 8) | (vo << 16) | (mat << 24);
+    }
+    const uint32_t v = odd ? vo : ve;
+    return v | 0xFF00u | (v << 16) | (mat << 24);
+}
+
 constexpr int kMaxLevels = 14;  // 2^14 = 16384 = largest grid side
 constexpr int kShift = 16;      // 2^16 fixed-point units per world unit
 constexpr int kThreads = 128;   // threads per trace block (4 warps)
@@ -55,10 +74,22 @@ constexpr uint8_t kFaceNX = 0, kFacePX = 1, kFaceNY = 2, kFacePY = 3, kFaceNZ = 
 struct WorldDev {
     const uint32_t *base;               // level 0 at base, level k at base + off[k]
     uint32_t off[kMaxLevels + 1];       // word offset of each level
-    uint32_t stride[kMaxLevels + 1];    // words per row of each level (= its width in nodes)
+    uint32_t stride[kMaxLevels + 1];    // width of each level in nodes (cells at level 0) = its
+                                        // words per row, except for paired texels (W / 2)
     uint32_t rows[kMaxLevels + 1];      // rows of each level (= its height in nodes)
     int32_t W, H, L;                    // grid size, top level
+    int32_t pair;                       // 1: level 0 holds paired 2-byte texels
 };
+
+#ifdef __CUDACC__
+// Node-form word of cell (x, y) of level 0, either storage.
+__device__ __forceinline__ uint32_t level0_node(const WorldDev &w, int32_t x, int32_t y) {
+    if (w.pair)
+        return pair_node(__ldg(w.base + (uint32_t)y * ((uint32_t)w.W >> 1) + ((uint32_t)x >> 1)),
+                         (uint32_t)x & 1);
+    return __ldg(w.base + (uint32_t)y * (uint32_t)w.W + (uint32_t)x);
+}
+#endif
 
 struct CamDev {
     int32_t o[3];
@@ -105,12 +136,13 @@ int launch_march_batched(const RenderParams &p, const MarchParams &m, int blocks
 int march_occupancy(int *blocks_per_sm);
 
 // Launch wrappers (hf_trace.cu)
+// The trace kernels are instantiated per level-0 storage; p.world.pair picks one.
 int launch_trace_batched(const RenderParams &p, bool shadows, bool stats, int blocks,
                          void *stream);
 int launch_trace_plain(const RenderParams &p, bool shadows, bool stats, uint32_t cam_index,
                        uint32_t n_tiles, void *stream);
-const void *trace_batched_fn(bool shadows, bool stats);
-int trace_batched_occupancy(bool shadows, bool stats, int *blocks_per_sm);
+const void *trace_batched_fn(bool shadows, bool stats, bool pair);
+int trace_batched_occupancy(bool shadows, bool stats, bool pair, int *blocks_per_sm);
 
 // What the allocation-free render needs to know about a context (hf_api.cpp).
 struct CtxView {

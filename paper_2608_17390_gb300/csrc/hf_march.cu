@@ -31,7 +31,7 @@ __device__ __forceinline__ MarchPoint march_solid(const WorldDev &w, float x, fl
     r.solid = false;
     r.layer = 0;
     if ((uint32_t)r.cx < (uint32_t)w.W && (uint32_t)r.cy < (uint32_t)w.H) {
-        const uint32_t c = __ldg(w.base + (uint32_t)r.cy * (uint32_t)w.W + (uint32_t)r.cx);
+        const uint32_t c = level0_node(w, r.cx, r.cy);
         const uint32_t h0 = c & 0xFF, h1 = (c >> 8) & 0xFF, h2 = (c >> 16) & 0xFF;
         const bool floor_ = z <= (float)h0;
         const bool upper = h2 > h0 && z >= (float)h1 && z <= (float)h2;  // node-form cell

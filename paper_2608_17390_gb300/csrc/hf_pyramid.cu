@@ -37,8 +37,20 @@ __device__ __forceinline__ uint32_t combine(uint32_t a, uint32_t b) {
            max(a & 0xFF0000u, b & 0xFF0000u);
 }
 
+// Child (x, y) of a level-1 node or of a higher one.  src_mode: 0 node words,
+// 1 level-0 cells in node form, 2 level-0 paired texels (rows of stride / 2
+// words, stride = width in cells).
+__device__ __forceinline__ uint32_t child_node(const uint32_t *src, uint32_t stride, int src_mode,
+                                               int32_t x, int32_t y) {
+    if (src_mode == 2)
+        return cell_node(pair_node(src[(uint32_t)y * (stride >> 1) + ((uint32_t)x >> 1)],
+                                   (uint32_t)x & 1));
+    const uint32_t c = src[(uint32_t)y * stride + (uint32_t)x];
+    return src_mode ? cell_node(c) : c;
+}
+
 __device__ __forceinline__ uint32_t reduce_children(const uint32_t *src, uint32_t stride,
-                                                    int32_t sw, int32_t sh, bool cells,
+                                                    int32_t sw, int32_t sh, int src_mode,
                                                     int32_t i, int32_t j) {
     uint32_t v = kIdentity;
 #pragma unroll
@@ -46,24 +58,21 @@ __device__ __forceinline__ uint32_t reduce_children(const uint32_t *src, uint32_
 #pragma unroll
         for (int dx = 0; dx < 2; ++dx) {
             const int32_t x = 2 * i + dx, y = 2 * j + dy;
-            if (x < sw && y < sh) {
-                uint32_t c = src[(uint32_t)y * stride + (uint32_t)x];
-                v = combine(v, cells ? cell_node(c) : c);
-            }
+            if (x < sw && y < sh) v = combine(v, child_node(src, stride, src_mode, x, y));
         }
     }
     return v;
 }
 
 __global__ void k_pyr_level(const uint32_t *__restrict__ src, uint32_t src_stride, int32_t sw,
-                            int32_t sh, int cells, uint32_t *__restrict__ dst,
+                            int32_t sh, int src_mode, uint32_t *__restrict__ dst,
                             uint32_t dst_stride, int32_t i0, int32_t j0, int32_t ni,
                             int64_t count) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= count) return;
     const int32_t i = i0 + (int32_t)(idx % ni), j = j0 + (int32_t)(idx / ni);
     dst[(uint32_t)j * dst_stride + (uint32_t)i] =
-        reduce_children(src, src_stride, sw, sh, cells != 0, i, j);
+        reduce_children(src, src_stride, sw, sh, src_mode, i, j);
 }
 
 // Levels k_from..L of a small rectangle in one block; __syncthreads orders
@@ -81,7 +90,7 @@ __global__ void __launch_bounds__(kTailThreads) k_pyr_tail(uint32_t *world, cons
         for (int32_t idx = threadIdx.x; idx < ni * nj; idx += blockDim.x) {
             const int32_t i = i0 + idx % ni, j = j0 + idx / ni;
             dst[(uint32_t)j * w.stride[k] + (uint32_t)i] =
-                reduce_children(src, w.stride[k - 1], sw, sh, k == 1, i, j);
+                reduce_children(src, w.stride[k - 1], sw, sh, k == 1 ? 1 + w.pair : 0, i, j);
         }
         __syncthreads();
     }
@@ -105,7 +114,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_pyr_build_tiles(uint32_t *wor
     const int32_t cx0 = bx + 4 * qx, cy0 = by + 4 * qy;
     const uint32_t *cells = world;  // level 0
     uint32_t c[4][4];
-    if (cx0 + 4 <= w.W && cy0 + 4 <= w.H && (w.W & 3) == 0) {
+    if (cx0 + 4 <= w.W && cy0 + 4 <= w.H && (w.W & 3) == 0 && !w.pair) {
         uint4 v[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r)  // four 16-byte loads issued before use
@@ -118,15 +127,29 @@ __global__ void __launch_bounds__(kBuildThreads) k_pyr_build_tiles(uint32_t *wor
             c[r][2] = cell_node(v[r].z);
             c[r][3] = cell_node(v[r].w);
         }
+    } else if (cx0 + 4 <= w.W && cy0 + 4 <= w.H && (w.W & 3) == 0) {
+        // paired texels: the 4 cells of a row are 2 pair words (8 bytes,
+        // aligned because W / 2 and cx0 / 2 are even)
+        uint2 v[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            v[r] = __ldg(reinterpret_cast<const uint2 *>(
+                cells + (uint32_t)(cy0 + r) * ((uint32_t)w.W >> 1) + ((uint32_t)cx0 >> 1)));
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            c[r][0] = cell_node(pair_node(v[r].x, 0));
+            c[r][1] = cell_node(pair_node(v[r].x, 1));
+            c[r][2] = cell_node(pair_node(v[r].y, 0));
+            c[r][3] = cell_node(pair_node(v[r].y, 1));
+        }
     } else {
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int32_t x = cx0 + q, y = cy0 + r;
-                c[r][q] = (x < w.W && y < w.H)
-                              ? cell_node(__ldg(cells + (uint32_t)y * (uint32_t)w.W + (uint32_t)x))
-                              : kIdentity;
+                c[r][q] = (x < w.W && y < w.H) ? child_node(cells, (uint32_t)w.W, 1 + w.pair, x, y)
+                                               : kIdentity;
             }
     }
     // levels 1 and 2 of the block in registers
@@ -217,7 +240,8 @@ int pyramid_repair_from(uint32_t *world, const WorldDev &w, int k_from, int32_t 
         const int threads = 256;
         const int64_t blocks = (count + threads - 1) / threads;
         k_pyr_level<<<(unsigned)blocks, threads, 0, s>>>(world + w.off[k - 1], w.stride[k - 1], sw,
-                                                         sh, k == 1, world + w.off[k],
+                                                         sh, k == 1 ? 1 + w.pair : 0,
+                                                         world + w.off[k],
                                                          w.stride[k], i0, j0, (int32_t)ni, count);
         if (cudaGetLastError() != cudaSuccess) return -1;
     }

@@ -190,7 +190,7 @@ __device__ __forceinline__ bool vertical_test(const Ray &r, uint32_t word, Hit &
 // is the midline of exactly one sub-level, so a ray that enters a cell through
 // its Y side while also crossing an X cell boundary (a corner) is detected on
 // the way down and reported with the X face.
-template <bool STATS>
+template <bool STATS, bool PAIR>
 __device__ __forceinline__ void trace_ray(const WorldDev &w, const LevelDev *lvt, const Ray &r,
                                           int start_level, int mip_start, int max_steps, Hit &h,
                                           Counters &cnt) {
@@ -203,7 +203,7 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const LevelDev *lvt
     if ((uint32_t)cx >= (uint32_t)w.W || (uint32_t)cy >= (uint32_t)w.H) return;
 
     if (adx == 0 && ady == 0) {
-        const uint32_t word = load_word(w, 0, cx, cy);
+        const uint32_t word = level0_node(w, cx, cy);
         if (STATS) cnt.cells++;
         if (vertical_test(r, word, h)) {
             h.cx = cx;
@@ -242,7 +242,11 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const LevelDev *lvt
         // segment's z range [zlo, zhi] misses (-inf, h0] and [h1, h2] exactly
         // when zlo > top, or zlo > h0 and zhi < h1)
         const LevelDev lv = lvt[level];
-        const uint32_t word = __ldg(lv.base + (uint32_t)ny * lv.stride + (uint32_t)nx);
+        const uint32_t word =
+            PAIR && level == 0
+                ? pair_node(__ldg(lv.base + (uint32_t)ny * (lv.stride >> 1) + ((uint32_t)nx >> 1)),
+                            (uint32_t)nx & 1)
+                : __ldg(lv.base + (uint32_t)ny * lv.stride + (uint32_t)nx);
         const uint32_t node = word;
         if (STATS) {
             if (level > 0) cnt.nodes++;
@@ -344,7 +348,7 @@ __device__ __forceinline__ void store_pixel(const RenderParams &p, const CamDev 
 
 // One pixel: its primary ray, then (with shadows) the shadow ray, which
 // reuses the same traversal loop and registers.
-template <bool SHADOWS, bool STATS>
+template <bool SHADOWS, bool STATS, bool PAIR>
 __device__ __forceinline__ void trace_pixel(const RenderParams &p, const LevelDev *lvt,
                                             const CamDev &c, int start,
                                             int32_t px, int32_t py, Counters &cnt,
@@ -365,9 +369,9 @@ __device__ __forceinline__ void trace_pixel(const RenderParams &p, const LevelDe
     for (;;) {
         Hit h;
         if (!SHADOWS || !shadow_pass) {
-            trace_ray<STATS>(p.world, lvt, r, start, p.mip_start, p.max_steps, h, cnt);
+            trace_ray<STATS, PAIR>(p.world, lvt, r, start, p.mip_start, p.max_steps, h, cnt);
         } else {
-            trace_ray<STATS>(p.world, lvt, r, min(kShadowStart, p.shadow_mip), p.shadow_mip,
+            trace_ray<STATS, PAIR>(p.world, lvt, r, min(kShadowStart, p.shadow_mip), p.shadow_mip,
                              p.max_steps, h, scnt);
         }
         if (h.face == kFaceError) err = true;
@@ -427,7 +431,7 @@ __device__ __forceinline__ int primary_start(const RenderParams &p, const CamDev
     if ((uint32_t)cx >= (uint32_t)w.W || (uint32_t)cy >= (uint32_t)w.H) return p.mip_start;
     bool above = false;
     if (lane <= p.mip_start) {
-        const uint32_t word = load_word(w, lane, cx >> lane, cy >> lane);
+        const uint32_t word = lane ? load_word(w, lane, cx >> lane, cy >> lane) : level0_node(w, cx, cy);
         const int32_t top = (word >> 16) & 0xFF;  // every level in node form
         above = c.o[2] > (top << kShift);
     }
@@ -436,7 +440,7 @@ __device__ __forceinline__ int primary_start(const RenderParams &p, const CamDev
 }
 
 // One warp renders one tile: lane l traces the tile's pixels l, l+32, ...
-template <bool SHADOWS, bool STATS>
+template <bool SHADOWS, bool STATS, bool PAIR>
 __device__ __forceinline__ void trace_tile(const RenderParams &p, const LevelDev *lvt,
                                            const CamDev &c, uint32_t local_tile, int lane) {
     const uint32_t tx = local_tile % c.tiles_x, ty = local_tile / c.tiles_x;
@@ -451,7 +455,7 @@ __device__ __forceinline__ void trace_tile(const RenderParams &p, const LevelDev
         const int32_t px = x0 + (i & ((1 << tw_log2) - 1));
         const int32_t py = y0 + (i >> tw_log2);
         if (px < (int32_t)c.w && py < (int32_t)c.h) {
-            trace_pixel<SHADOWS, STATS>(p, lvt, c, start, px, py, cnt, scnt, nshadow, err);
+            trace_pixel<SHADOWS, STATS, PAIR>(p, lvt, c, start, px, py, cnt, scnt, nshadow, err);
             if (STATS) nrays++;
         }
     }
@@ -472,6 +476,8 @@ __device__ __forceinline__ void trace_tile(const RenderParams &p, const LevelDev
     }
 }
 
+// stride of level 0 is its width in cells also for paired texels (whose rows
+// then hold stride / 2 words)
 __device__ __forceinline__ void fill_levels(LevelDev *s_lv, const WorldDev &w) {
     const int k = threadIdx.x;
     if (k <= w.L) s_lv[k] = LevelDev{w.base + w.off[k], (uint32_t)w.stride[k], (uint32_t)w.rows[k]};
@@ -492,7 +498,7 @@ __device__ __forceinline__ const CamDev &stage_cam(CamDev *slot, const CamDev *c
 
 // Persistent batched kernel: warps pop (camera, tile) items from one atomic
 // counter until the batch is drained.  One launch renders every camera.
-template <bool SHADOWS, bool STATS>
+template <bool SHADOWS, bool STATS, bool PAIR>
 __global__ void __launch_bounds__(kThreads, HF_TRACE_MIN_BLOCKS) k_trace_batched(const RenderParams p) {
     __shared__ uint32_t s_base[kMaxCams + 1];
     __shared__ CamDev s_cam[kThreads / 32];
@@ -516,12 +522,12 @@ __global__ void __launch_bounds__(kThreads, HF_TRACE_MIN_BLOCKS) k_trace_batched
             else hi = mid;
         }
         const CamDev &c = stage_cam(&s_cam[threadIdx.x >> 5], p.cams, lo, lane);
-        trace_tile<SHADOWS, STATS>(p, s_lv, c, t - s_base[lo], lane);
+        trace_tile<SHADOWS, STATS, PAIR>(p, s_lv, c, t - s_base[lo], lane);
     }
 }
 
 // Plain kernel: one camera, one warp per tile, grid covers the image once.
-template <bool SHADOWS, bool STATS>
+template <bool SHADOWS, bool STATS, bool PAIR>
 __global__ void __launch_bounds__(kThreads, HF_TRACE_MIN_BLOCKS) k_trace_plain(const RenderParams p, uint32_t cam,
                                                           uint32_t n_tiles) {
     __shared__ CamDev s_cam[kThreads / 32];
@@ -532,38 +538,45 @@ __global__ void __launch_bounds__(kThreads, HF_TRACE_MIN_BLOCKS) k_trace_plain(c
     if (t >= n_tiles) return;
     const int lane = threadIdx.x & 31;
     const CamDev &c = stage_cam(&s_cam[threadIdx.x >> 5], p.cams, cam, lane);
-    trace_tile<SHADOWS, STATS>(p, s_lv, c, t, lane);
+    trace_tile<SHADOWS, STATS, PAIR>(p, s_lv, c, t, lane);
 }
 
-template <bool SH, bool ST>
+template <bool SH, bool ST, bool PA>
 const void *batched_ptr() {
-    return reinterpret_cast<const void *>(&k_trace_batched<SH, ST>);
+    return reinterpret_cast<const void *>(&k_trace_batched<SH, ST, PA>);
+}
+
+template <bool PA>
+const void *batched_fn(bool shadows, bool stats) {
+    if (shadows) return stats ? batched_ptr<true, true, PA>() : batched_ptr<true, false, PA>();
+    return stats ? batched_ptr<false, true, PA>() : batched_ptr<false, false, PA>();
+}
+
+template <bool SH, bool ST, bool PA>
+void plain_launch(const RenderParams &p, uint32_t blocks, cudaStream_t s, uint32_t cam,
+                  uint32_t n_tiles) {
+    k_trace_plain<SH, ST, PA><<<blocks, kThreads, 0, s>>>(p, cam, n_tiles);
 }
 
 }  // namespace
 
-const void *trace_batched_fn(bool shadows, bool stats) {
-    if (shadows) return stats ? batched_ptr<true, true>() : batched_ptr<true, false>();
-    return stats ? batched_ptr<false, true>() : batched_ptr<false, false>();
+const void *trace_batched_fn(bool shadows, bool stats, bool pair) {
+    return pair ? batched_fn<true>(shadows, stats) : batched_fn<false>(shadows, stats);
 }
 
-int trace_batched_occupancy(bool shadows, bool stats, int *blocks_per_sm) {
+int trace_batched_occupancy(bool shadows, bool stats, bool pair, int *blocks_per_sm) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        blocks_per_sm, trace_batched_fn(shadows, stats), kThreads, 0);
+        blocks_per_sm, trace_batched_fn(shadows, stats, pair), kThreads, 0);
     return e == cudaSuccess ? 0 : -1;
 }
 
 int launch_trace_batched(const RenderParams &p, bool shadows, bool stats, int blocks,
                          void *stream) {
-    cudaStream_t s = (cudaStream_t)stream;
-    if (shadows) {
-        if (stats) k_trace_batched<true, true><<<blocks, kThreads, 0, s>>>(p);
-        else k_trace_batched<true, false><<<blocks, kThreads, 0, s>>>(p);
-    } else {
-        if (stats) k_trace_batched<false, true><<<blocks, kThreads, 0, s>>>(p);
-        else k_trace_batched<false, false><<<blocks, kThreads, 0, s>>>(p);
-    }
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    void *args[] = {const_cast<RenderParams *>(&p)};
+    const cudaError_t e =
+        cudaLaunchKernel(trace_batched_fn(shadows, stats, p.world.pair != 0), dim3(blocks),
+                         dim3(kThreads), args, 0, (cudaStream_t)stream);
+    return e == cudaSuccess ? 0 : -1;
 }
 
 int launch_trace_plain(const RenderParams &p, bool shadows, bool stats, uint32_t cam,
@@ -572,13 +585,13 @@ int launch_trace_plain(const RenderParams &p, bool shadows, bool stats, uint32_t
     cudaStream_t s = (cudaStream_t)stream;
     const uint32_t warps = kThreads / 32;
     const uint32_t blocks = (n_tiles + warps - 1) / warps;
-    if (shadows) {
-        if (stats) k_trace_plain<true, true><<<blocks, kThreads, 0, s>>>(p, cam, n_tiles);
-        else k_trace_plain<true, false><<<blocks, kThreads, 0, s>>>(p, cam, n_tiles);
-    } else {
-        if (stats) k_trace_plain<false, true><<<blocks, kThreads, 0, s>>>(p, cam, n_tiles);
-        else k_trace_plain<false, false><<<blocks, kThreads, 0, s>>>(p, cam, n_tiles);
-    }
+    using Fn = void (*)(const RenderParams &, uint32_t, cudaStream_t, uint32_t, uint32_t);
+    static const Fn table[8] = {
+        plain_launch<false, false, false>, plain_launch<false, false, true>,
+        plain_launch<false, true, false>,  plain_launch<false, true, true>,
+        plain_launch<true, false, false>,  plain_launch<true, false, true>,
+        plain_launch<true, true, false>,   plain_launch<true, true, true>};
+    table[(shadows ? 4 : 0) + (stats ? 2 : 0) + (p.world.pair ? 1 : 0)](p, blocks, s, cam, n_tiles);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -137,3 +137,35 @@ def test_camera_dtype_matches_c_layout(hf):
     assert synth.CAMERA_DTYPE == hf.CAMERA_DTYPE
     assert ctypes.sizeof(hf.hf_outputs) == 48
     assert ctypes.sizeof(hf.hf_render_opts) == 40
+
+
+def test_pair_validation_agrees_with_the_oracle(hf):
+    """The library's paired-texel check and the oracle's decoder-side check
+    accept and reject the same grids, at the same first bad pair."""
+    import json
+
+    from oracle import pairs as opairs
+
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "pair_codec.json")))
+    for case in g["valid"] + g["invalid"]:
+        t = np.array(case["texels"], dtype=np.uint16)
+        ok, bad = opairs.validate(t)
+        rc, lbad = hf.hf_validate_pairs(t)
+        assert (rc == hf.HF_OK) == ok and lbad == bad, case["name"]
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        t = rng.integers(0, 1 << 16, (3, 4)).astype(np.uint16)
+        t[:, 0::2] &= 0x87FF  # keep many pairs near the valid set
+        t[:, 1::2] &= 0x87FF
+        ok, bad = opairs.validate(t)
+        rc, lbad = hf.hf_validate_pairs(t)
+        assert (rc == hf.HF_OK) == ok and lbad == bad
+
+
+def test_create_pairs_rejects_before_touching_the_gpu(hf):
+    for t in (np.zeros((4, 3), np.uint16),                       # odd width
+              np.array([[5 | (0x80 << 8), 100]], np.uint16),     # flag on one texel
+              np.zeros((0, 4), np.uint16)):
+        with pytest.raises(hf.HFError) as e:
+            hf.hf_create_pairs(t)
+        assert e.value.code == hf.HF_E_INVALID_ARG

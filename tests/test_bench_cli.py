@@ -12,14 +12,19 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
 
-@pytest.mark.parametrize("name", ["c1", "c2", "c3", "c4"])
+@pytest.mark.parametrize("name", ["c1", "c2", "c3", "c4", "c4pair"])
 def test_workloads_build(name):
     import bench
 
     wl = bench.workload(name, frames_per_step=7)
     assert wl["cells"].ndim == 2 and len(wl["cams"]) >= 1 and wl["name"]
-    if name == "c4":
+    if name.startswith("c4"):
         assert "7 frames" in wl["name"] and len(wl["cams"]) == 1000
+    if name == "c4pair":
+        from oracle import pairs
+
+        assert wl["texels"].nbytes == 64 << 20
+        assert (pairs.decode(wl["texels"]) == wl["cells"]).all()
 
 
 def test_reference_arm_line():
