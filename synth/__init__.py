@@ -26,6 +26,7 @@ from .terrain import (
     crater_edit,
 )
 from .pairs import pairify, encode_pairs
+from .scatter import footprint_for, footprints
 from .cameras import (
     CAMERA_DTYPE,
     pose_to_camera,
