@@ -600,13 +600,10 @@ def run_protocol(args):
     ev_ms(frame, 24)
     res = {"exact": {"frame_ms": ev_ms(frame, 40), "batch12_ms": ev_ms(batch, 10)}}
     ref = [{k: v.cpu().numpy() for k, v in o.items()} for o in outs]
-    for st in (16, 64, 128, 256):
-        mo = hf.make_march_opts(steps=st, far_dist=600.0, stream=stream.cuda_stream)
-        mframe = lambda r: hf.hf_render_march(ctx, cams[r % 12:r % 12 + 1],
-                                              outs[r % 12:r % 12 + 1], mo)
-        mbatch = lambda r: hf.hf_render_march(ctx, cams, outs, mo)
-        ev_ms(mframe, 24)
-        row = {"frame_ms": ev_ms(mframe, 40), "batch12_ms": ev_ms(mbatch, 10)}
+
+    def by_pitch():
+        """Section 4.2 metrics of the current outputs against the exact cast
+        (clipped at the same far distance), averaged over the views of a pitch."""
         got = [{k: v.cpu().numpy() for k, v in o.items()} for o in outs]
         per_pitch = {}
         for p_i, pitch in enumerate(synth.PROTOCOL_PITCHES):
@@ -615,18 +612,40 @@ def run_protocol(args):
                 i = 3 * p_i + v
                 h, w = int(cams[i]["h"]), int(cams[i]["w"])
                 rd = ref[i]["depth"].reshape(h, w).astype(np.float64)
-                rh = np.isfinite(rd) & (rd <= 600.0)  # the exact cast, clipped at the same far distance
+                rh = np.isfinite(rd) & (rd <= 600.0)
                 gd = got[i]["depth"].reshape(h, w).astype(np.float64)
                 ms.append(metrics.compare(rh, rd, np.isfinite(gd), gd))
             per_pitch["%d" % int(pitch)] = {k: float(np.mean([m[k] for m in ms])) for k in ms[0]}
-        row["metrics_by_pitch"] = per_pitch
+        return per_pitch
+
+    for st in (16, 64, 128, 256):
+        mo = hf.make_march_opts(steps=st, far_dist=600.0, stream=stream.cuda_stream)
+        mframe = lambda r: hf.hf_render_march(ctx, cams[r % 12:r % 12 + 1],
+                                              outs[r % 12:r % 12 + 1], mo)
+        mbatch = lambda r: hf.hf_render_march(ctx, cams, outs, mo)
+        ev_ms(mframe, 24)
+        row = {"frame_ms": ev_ms(mframe, 40), "batch12_ms": ev_ms(mbatch, 10)}
+        row["metrics_by_pitch"] = by_pitch()
         res["march_%d" % st] = row
+    # the paper's Scattered method at three densities (footprint samples across x
+    # along x points per column interval), scored the same way
+    fps = synth.footprints(cams, far=600.0)
+    for nu, nv, nz in ((512, 512, 8), (1024, 1024, 16), (2048, 2048, 32)):
+        so = hf.make_scatter_opts(nu=nu, nv=nv, nz=nz, depth_max=1024.0, stream=stream.cuda_stream)
+        sframe = lambda r: hf.hf_render_scatter(ctx, cams[r % 12:r % 12 + 1], outs[r % 12:r % 12 + 1],
+                                                fps[r % 12:r % 12 + 1], so)
+        sbatch = lambda r: hf.hf_render_scatter(ctx, cams, outs, fps, so)
+        ev_ms(sframe, 24)
+        row = {"frame_ms": ev_ms(sframe, 40), "batch12_ms": ev_ms(sbatch, 10),
+               "footprint_samples": nu * nv, "points_per_column_interval": nz,
+               "metrics_by_pitch": by_pitch()}
+        res["scatter_%dx%dx%d" % (nu, nv, nz)] = row
     hf.hf_destroy(ctx)
     line = {"metric": "frame time, paper protocol (12 views, 1280x800): exact cast vs the "
-                      "paper's fixed-step march, with Section 4.2 metrics of the march",
+                      "paper's fixed-step march and Scattered method, with Section 4.2 metrics",
             "value": res["exact"]["frame_ms"], "unit": "ms per 1280x800 frame (exact cast)",
             "n_gpus": 1, "steps": 40, "warmup": 24, "higher_is_better": False,
-            "vs_baseline": None, "dtype": "i32 (exact) / f32 (march)", "data": "synthetic",
+            "vs_baseline": None, "dtype": "i32 (exact) / f32 (march, scatter)", "data": "synthetic",
             "config": {"workload": "2048x16384 grid (seed 4, 30% slabs), 3 views at each pitch "
                                    "0/-30/-60/-90, 1280x800, hfov 75, far 600 (march); "
                                    "steady-state frames, primary rays only"},

@@ -68,6 +68,7 @@ extern "C" {
 #define HF_STATS 8u   /* count node and cell fetches (read back with hf_stats) */
 #define HF_NOGRAPH 16u /* launch directly instead of replaying a captured CUDA graph */
 #define HF_NOWAIT 32u /* return HF_E_BUSY instead of waiting for a free render slot */
+#define HF_SCATTER_RAW 128u /* hf_render_scatter: leave the packed words in hit_cell, no resolve */
 #define HF_HOST_OUTPUTS 64u /* the output buffers are pinned HOST memory (cudaHostAlloc or
                                cudaHostRegister): the kernel writes the results there itself,
                                over the host link, with no separate copy (hf_render only) */
@@ -247,6 +248,56 @@ typedef struct {
     uint32_t flags;          /* HF_SYNC */
     void *cuda_stream;       /* NULL = the context's stream */
 } hf_march_opts;
+
+/* The paper's Scattered method (Section 3: its object-order painter recast as a
+ * parallel atomic scatter), as a comparison renderer.  Per camera, an nu x nv
+ * grid of samples covers a camera-aligned ground footprint: longitudinal s
+ * along the horizontal direction 90 degrees left of the camera's right vector,
+ * s = s_lo + (s_hi - s_lo) t^2 with t = (j + 0.5) / nv (samples crowd near the
+ * camera end), lateral u along the right vector, |u| <= u_min + k_lat |s| (a
+ * trapezoid, like a pitched camera's view of the ground).
+ * Each sample walks its cell's column (nz points from the floor top down to 0,
+ * and for a slab nz points from its top down to its underside), projects every
+ * point with the camera (d = F + aR + bU, pixel (floor((a + w)/2), floor((h -
+ * b)/2)), points behind or outside dropped) and keeps per pixel, with a 32-bit
+ * atomicMin, the least (24-bit quantised Euclidean depth << 8 | material |
+ * layer << 3).  The resolve writes depth, the cell under the reconstructed
+ * point, layer, face +Z and the material's colour lit from above; pixels no
+ * point reached are misses.  float32 arithmetic in a fixed order: results are
+ * reproducible bit for bit.  Approximate by design (gaps where the footprint is
+ * sparse; the paper's coherence metric measures them). */
+typedef struct {
+    float s_lo, s_hi; /* longitudinal range (world units), s_hi > s_lo */
+    float k_lat;      /* growth of the lateral half-width per unit of |s| */
+    float u_min;      /* lateral half-width at s = 0 */
+} hf_footprint;
+
+typedef struct {
+    uint32_t nu, nv;    /* footprint samples across and along (<= 8192 each); 0 = 1024 */
+    uint32_t nz;        /* points per column interval (2..4096); 0 = 16 */
+    uint32_t flags;     /* HF_SYNC | HF_SCATTER_RAW */
+    float depth_max;    /* depth quantisation range, world units (2^24 steps); 0 = 1024 */
+    int32_t sun[3];     /* as in hf_render_opts */
+    void *cuda_stream;  /* NULL = the context's stream */
+} hf_scatter_opts;
+
+/* A footprint that bounds what the camera can see: a 5 x 5 grid of image rays
+ * followed to the plane z = 0 or to far_dist; the s range bounds their ground
+ * points; k_lat is the growth of the widest |u| from the image's bottom row of
+ * points to its top row per unit of s (0 if it shrinks); u_min is then the
+ * least value that holds every point; 5 % margins.  Host only.
+ * Errors: HF_E_INVALID_ARG (null, far_dist <= 0, a right vector with no
+ * horizontal part). */
+int hf_scatter_footprint(const hf_camera *cam, float far_dist, hf_footprint *out);
+
+/* Scatter-render n cameras into outs (DEVICE buffers; hit_cell is required: it
+ * is the screen buffer the atomics target, then the resolved cell index).
+ * fps: n footprints (HOST), or NULL for hf_scatter_footprint(cam, 600).
+ * Asynchronous on the render stream unless HF_SYNC; ordered after edits like
+ * hf_render.  Errors: HF_E_INVALID_ARG (null, n > HF_MAX_CAMERAS, invalid
+ * camera or footprint, missing hit_cell, bad densities), HF_E_CUDA. */
+int hf_render_scatter(hf_ctx *ctx, const hf_camera *cams, uint32_t n, const hf_footprint *fps,
+                      const hf_outputs *outs, const hf_scatter_opts *opts);
 
 /* The paper's own height-field ray march (Section 3.1), for comparison with
  * the exact cast: per pixel ray, clip the segment at the far distance and, for

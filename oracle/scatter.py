@@ -15,7 +15,9 @@ O the origin in 2^-16 units):
 Footprint sample (i, j), 0 <= i < nu, 0 <= j < nv (the "warped footprint"):
   t = (j + 0.5) / nv;  s = s_lo + (s_hi - s_lo) * (t * t)   (quadratic warp:
       samples crowd near s_lo, the camera end of the footprint)
-  half = max(u_min, |s| * k_lat);  u = half * (((i + 0.5) / nu) * 2 - 1)
+  half = u_min + |s| * k_lat;  u = half * (((i + 0.5) / nu) * 2 - 1)
+  (a trapezoid: a pitched camera's view of the ground widens linearly with
+  distance from a non-zero width at its near edge)
   x = (Of_x + s*fh_x) + u*rh_x;  y = (Of_y + s*fh_y) + u*rh_y
   the cell (floor x, floor y) (skipped outside the grid) gives the column.
 Column walk, m = 0 .. nz-1, tm = m / (nz - 1):
@@ -70,7 +72,7 @@ def footprint(k, nu, nv, s_lo, s_hi, k_lat, u_min):
     i = np.arange(nu, dtype=f32)[None, :]
     t = (j + f32(0.5)) / f32(nv)
     s = f32(s_lo) + (f32(s_hi) - f32(s_lo)) * (t * t)
-    half = np.maximum(f32(u_min), np.abs(s) * f32(k_lat))
+    half = f32(u_min) + np.abs(s) * f32(k_lat)
     u = half * (((i + f32(0.5)) / f32(nu)) * f32(2.0) - f32(1.0))
     x = (k["Of"][0] + s * k["fh"][0]) + u * k["rh"][0]
     y = (k["Of"][1] + s * k["fh"][1]) + u * k["rh"][1]

@@ -41,6 +41,7 @@ HF_STATS = 8
 HF_NOGRAPH = 16
 HF_NOWAIT = 32
 HF_HOST_OUTPUTS = 64
+HF_SCATTER_RAW = 128
 HF_MIP_AUTO = 0xFFFFFFFF
 HF_MAX_DIM = 16384
 HF_MAX_CAMERAS = 4096
@@ -93,6 +94,17 @@ class hf_march_opts(ctypes.Structure):
                 ("cuda_stream", ctypes.c_void_p)]
 
 
+class hf_footprint(ctypes.Structure):
+    _fields_ = [("s_lo", ctypes.c_float), ("s_hi", ctypes.c_float), ("k_lat", ctypes.c_float),
+                ("u_min", ctypes.c_float)]
+
+
+class hf_scatter_opts(ctypes.Structure):
+    _fields_ = [("nu", ctypes.c_uint32), ("nv", ctypes.c_uint32), ("nz", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32), ("depth_max", ctypes.c_float),
+                ("sun", ctypes.c_int32 * 3), ("cuda_stream", ctypes.c_void_p)]
+
+
 class hf_info_t(ctypes.Structure):
     _fields_ = [("width", ctypes.c_uint32), ("height", ctypes.c_uint32),
                 ("levels", ctypes.c_uint32), ("render_slots", ctypes.c_uint32),
@@ -121,6 +133,8 @@ _SIGS = {
     "hf_render": ([_P, _P, _U32, _P, ctypes.POINTER(hf_render_opts)], ctypes.c_int),
     "hf_render_noalloc": ([_P, _P, _U32, _P, ctypes.POINTER(hf_render_opts)], ctypes.c_int),
     "hf_render_march": ([_P, _P, _U32, _P, ctypes.POINTER(hf_march_opts)], ctypes.c_int),
+    "hf_render_scatter": ([_P, _P, _U32, _P, _P, ctypes.POINTER(hf_scatter_opts)], ctypes.c_int),
+    "hf_scatter_footprint": ([_P, ctypes.c_float, ctypes.POINTER(hf_footprint)], ctypes.c_int),
     "hf_sync": ([_P], ctypes.c_int),
     "hf_destroy": ([_P], ctypes.c_int),
     "hf_camera_from_pose": ([ctypes.c_double] * 6 + [_U32, _U32, ctypes.POINTER(hf_camera)],
@@ -275,6 +289,38 @@ def hf_render_noalloc(ctx, cams, outs, opts=None):
     popts = ctypes.byref(opts) if opts is not None else None
     _check(lib.hf_render_noalloc(ctx, recs.ctypes.data if n else None, n, oarr, popts),
            "hf_render_noalloc")
+
+
+def make_scatter_opts(nu=0, nv=0, nz=0, flags=0, depth_max=0.0, sun=(0, 0, 0), stream=None):
+    return hf_scatter_opts(nu, nv, nz, flags, depth_max, (ctypes.c_int32 * 3)(*sun), stream)
+
+
+def hf_scatter_footprint(cam, far_dist=600.0):
+    """(s_lo, s_hi, k_lat, u_min) the library chooses for one camera record."""
+    rec = camera_records(np.asarray([cam]))
+    c = hf_camera.from_buffer_copy(rec.tobytes())
+    f = hf_footprint()
+    _check(lib.hf_scatter_footprint(ctypes.byref(c), far_dist, ctypes.byref(f)),
+           "hf_scatter_footprint")
+    return (f.s_lo, f.s_hi, f.k_lat, f.u_min)
+
+
+def hf_render_scatter(ctx, cams, outs, footprints=None, opts=None):
+    """The paper's Scattered method (comparison renderer; see include/hf.h).
+    footprints: float32 [n, 4] (s_lo, s_hi, k_lat, u_min) or None for the
+    library's; outs need hit_cell (the screen buffer)."""
+    recs = camera_records(cams)
+    n = len(recs)
+    if len(outs) != n:
+        raise ValueError("one output set per camera")
+    oarr = _outputs_array(outs)
+    fp = None
+    if footprints is not None:
+        fp = np.ascontiguousarray(footprints, dtype=np.float32).reshape(n, 4)
+    popts = ctypes.byref(opts) if opts is not None else None
+    _check(lib.hf_render_scatter(ctx, recs.ctypes.data if n else None, n,
+                                 fp.ctypes.data if fp is not None else None, oarr, popts),
+           "hf_render_scatter")
 
 
 def make_march_opts(steps=0, bisections=0, far_dist=0.0, tile_w=0, tile_h=0, flags=0,

@@ -12,6 +12,7 @@
 //   * a render on a foreign stream first waits for the last edit's event.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -681,7 +682,7 @@ static void *device_alias(void *ptr) {
 
 static int prepare_batch(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_outputs *outs,
                          uint32_t tw, uint32_t th, bool nowait, void *user_stream, Batch &b,
-                         bool host_outputs = false) {
+                         bool host_outputs = false, size_t extra_bytes = 0) {
     const int twl = ilog2_exact(tw), thl = ilog2_exact(th);
     if (twl < 0 || thl < 0 || tw * th < 32 || tw * th > 256 || tw > 256 || th > 256)
         return HF_E_INVALID_ARG;
@@ -697,7 +698,7 @@ static int prepare_batch(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_
     int rc = acquire_slot(c, nowait, &b.slot);
     if (rc != HF_OK) return rc;
     Slot &s = c->slots[b.slot];
-    b.bytes = sizeof(hf::BatchHeader) + (size_t)n * sizeof(hf::CamDev);
+    b.bytes = sizeof(hf::BatchHeader) + (size_t)n * sizeof(hf::CamDev) + extra_bytes;
     b.bucket = (b.bytes + kScratchAlign - 1) & ~(kScratchAlign - 1);
     rc = ensure_slot_cap(s, b.bucket);
     if (rc != HF_OK) return rc;
@@ -847,6 +848,113 @@ int hf_render_march(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_outpu
     Slot &s = c->slots[b.slot];
     CK(cudaMemcpyAsync(s.d_scratch, s.h_staging, b.bytes, cudaMemcpyHostToDevice, b.stream));
     if (hf::launch_march_batched(b.p, m, c->sm_count * c->occ_march, b.stream)) return HF_E_CUDA;
+    return finish_batch(c, b, (o.flags & HF_SYNC) != 0);
+}
+
+int hf_scatter_footprint(const hf_camera *cam, float far_dist, hf_footprint *out) {
+    if (!cam || !out || !(far_dist > 0.0f) || cam->w == 0 || cam->h == 0) return HF_E_INVALID_ARG;
+    const double S = 65536.0;
+    const double O[3] = {cam->origin[0] / S, cam->origin[1] / S, cam->origin[2] / S};
+    const double rl = std::hypot((double)cam->right[0], (double)cam->right[1]);
+    if (rl == 0.0) return HF_E_INVALID_ARG;
+    const double rh[2] = {cam->right[0] / rl, cam->right[1] / rl}, fh[2] = {-rh[1], rh[0]};
+    const double margin = 1.05;
+    double ss[25], uu[25], rows[25];
+    int np_ = 0;
+    for (int ia = 0; ia < 5; ++ia)
+        for (int ib = 0; ib < 5; ++ib) {  // a 5 x 5 grid of image points, edges included
+            const double fa = -1.0 + 0.5 * ia, fb = -1.0 + 0.5 * ib;
+            double d[3];
+            for (int k = 0; k < 3; ++k)
+                d[k] = cam->fwd[k] + fa * (cam->w - 1.0) * cam->right[k] + fb * (cam->h - 1.0) * cam->up[k];
+            const double dl = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            double t = far_dist / dl;
+            if (d[2] < 0) t = std::min(t, O[2] / -d[2]);  // to the plane z = 0
+            const double px = d[0] * t, py = d[1] * t;
+            ss[np_] = px * fh[0] + py * fh[1];
+            uu[np_] = std::fabs(px * rh[0] + py * rh[1]);
+            rows[np_] = fb;
+            ++np_;
+        }
+    double s_min = 0.0, s_max = -1e300, st = 0.0, sb = 0.0, ut = 0.0, ub = 0.0;
+    for (int i = 0; i < np_; ++i) {
+        s_min = std::min(s_min, ss[i]);
+        s_max = std::max(s_max, ss[i]);
+        if (rows[i] == 1.0) {  // top row of image points
+            st += ss[i] / 5.0;
+            ut = std::max(ut, uu[i]);
+        } else if (rows[i] == -1.0) {  // bottom row
+            sb += ss[i] / 5.0;
+            ub = std::max(ub, uu[i]);
+        }
+    }
+    const double ds = st - sb;
+    const double k_lat = ds != 0.0 ? std::max(0.0, (ut - ub) / ds) : 0.0;
+    double u0 = -1e300;
+    for (int i = 0; i < np_; ++i) u0 = std::max(u0, uu[i] - k_lat * std::fabs(ss[i]));
+    out->s_lo = (float)(s_min * margin - 1.0);
+    out->s_hi = (float)std::max(1.0, s_max * margin + 1.0);
+    out->k_lat = (float)(k_lat * margin);
+    out->u_min = (float)(std::max(u0 * margin, 0.0) + 1.0);
+    return HF_OK;
+}
+
+int hf_render_scatter(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_footprint *fps,
+                      const hf_outputs *outs, const hf_scatter_opts *opts) {
+    if (!c) return HF_E_INVALID_ARG;
+    if (n == 0) return HF_OK;
+    if (!cams || !outs || n > HF_MAX_CAMERAS) return HF_E_INVALID_ARG;
+    hf_scatter_opts o{};
+    if (opts) o = *opts;
+    hf::ScatterParams sp{};
+    sp.nu = o.nu ? o.nu : 1024;
+    sp.nv = o.nv ? o.nv : 1024;
+    sp.nz = o.nz ? o.nz : 16;
+    sp.depth_max = o.depth_max != 0.0f ? o.depth_max : 1024.0f;
+    sp.raw = (o.flags & HF_SCATTER_RAW) ? 1 : 0;
+    if (sp.nu > 8192 || sp.nv > 8192 || sp.nz < 2 || sp.nz > 4096 || !(sp.depth_max > 0.0f))
+        return HF_E_INVALID_ARG;
+    int32_t sun[3] = {o.sun[0], o.sun[1], o.sun[2]};
+    if (sun[0] == 0 && sun[1] == 0 && sun[2] == 0)
+        for (int i = 0; i < 3; ++i) sun[i] = kDefaultSun[i];
+    for (int i = 0; i < 3; ++i)
+        if (iabs64(sun[i]) >= kLimit21) return HF_E_INVALID_ARG;
+    // the resolved colour of each material: an up-facing surface lit by the sun
+    static const float albedo[8][3] = HF_ALBEDO_TABLE;
+    const double sl = std::sqrt((double)sun[0] * sun[0] + (double)sun[1] * sun[1] + (double)sun[2] * sun[2]);
+    const double kl = hf::kAmbient + hf::kDiffuse * std::max(0.0, sun[2] / sl);
+    for (int m = 0; m < 8; ++m) {
+        uint32_t rgba = 0xFF000000u;
+        for (int ch = 0; ch < 3; ++ch) {
+            const double v = std::min(1.0, std::max(0.0, (double)albedo[m][ch] * kl));
+            rgba |= (uint32_t)std::floor(255.0 * v + 0.5) << (8 * ch);
+        }
+        sp.colour[m] = rgba;
+    }
+    std::vector<hf_footprint> fp(n);
+    uint32_t maxpix = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        if (!outs[i].hit_cell) return HF_E_INVALID_ARG;  // the screen buffer
+        if (fps) {
+            fp[i] = fps[i];
+            if (!(fp[i].s_hi > fp[i].s_lo) || !(fp[i].k_lat >= 0.0f) || !(fp[i].u_min >= 0.0f))
+                return HF_E_INVALID_ARG;
+        } else if (hf_scatter_footprint(&cams[i], 600.0f, &fp[i]) != HF_OK) {
+            return HF_E_INVALID_ARG;
+        }
+        if (cams[i].right[0] == 0 && cams[i].right[1] == 0) return HF_E_INVALID_ARG;
+        maxpix = std::max(maxpix, cams[i].w * cams[i].h);
+    }
+    sp.max_pixels = maxpix;
+    Batch b;
+    int rc = prepare_batch(c, cams, n, outs, 8, 4, false, o.cuda_stream, b, false,
+                           (size_t)n * sizeof(hf_footprint));
+    if (rc != HF_OK) return rc;
+    Slot &s = c->slots[b.slot];
+    std::memcpy((char *)s.h_staging + sizeof(hf::BatchHeader) + (size_t)n * sizeof(hf::CamDev),
+                fp.data(), (size_t)n * sizeof(hf_footprint));
+    CK(cudaMemcpyAsync(s.d_scratch, s.h_staging, b.bytes, cudaMemcpyHostToDevice, b.stream));
+    if (hf::launch_scatter(b.p, sp, n, b.stream)) return HF_E_CUDA;
     return finish_batch(c, b, (o.flags & HF_SYNC) != 0);
 }
 

@@ -51,6 +51,14 @@ __host__ __device__ inline uint32_t pair_node(uint32_t pw, uint32_t odd) {
     return v | 0xFF00u | (v << 16) | (mat << 24);
 }
 
+// Shading (this library's fixed choice; the paper names its terms only): an
+// 8-entry albedo table by material, ambient 0.3, diffuse 0.7, a sky colour.
+#define HF_ALBEDO_TABLE                                                                     \
+    {{0.55f, 0.50f, 0.40f}, {0.35f, 0.55f, 0.25f}, {0.60f, 0.60f, 0.62f}, {0.80f, 0.72f, 0.50f}, \
+     {0.30f, 0.30f, 0.32f}, {0.70f, 0.35f, 0.20f}, {0.90f, 0.90f, 0.95f}, {0.25f, 0.40f, 0.60f}}
+constexpr float kAmbient = 0.3f, kDiffuse = 0.7f;
+constexpr uint32_t kSkyColour = 0xFFEBB487u;  // r 135, g 180, b 235, a 255
+
 constexpr int kMaxLevels = 14;  // 2^14 = 16384 = largest grid side
 constexpr int kShift = 16;      // 2^16 fixed-point units per world unit
 constexpr int kThreads = 128;   // threads per trace block (4 warps)
@@ -134,6 +142,18 @@ struct MarchParams {
 };
 int launch_march_batched(const RenderParams &p, const MarchParams &m, int blocks, void *stream);
 int march_occupancy(int *blocks_per_sm);
+
+// Parameters of the scattered comparison renderer (hf_scatter.cu).  The
+// per-camera footprints (float4: s_lo, s_hi, k_lat, u_min) follow the camera
+// table in the slot scratch.
+struct ScatterParams {
+    uint32_t nu, nv, nz;     // footprint samples across and along; points per column interval
+    uint32_t max_pixels;     // largest w * h of the batch
+    float depth_max;         // depth quantisation range (world units)
+    uint32_t colour[8];      // resolved colour per material (an up-facing, lit surface)
+    int32_t raw;             // 1: leave the packed words in hit_cell, no resolve
+};
+int launch_scatter(const RenderParams &p, const ScatterParams &s, uint32_t n_cams, void *stream);
 
 // Launch wrappers (hf_trace.cu)
 // The trace kernels are instantiated per level-0 storage; p.world.pair picks one.

@@ -32,12 +32,9 @@ namespace {
 #define HF_TRACE_MIN_BLOCKS 6  // resident blocks per SM asked of the register allocator (<= 80 registers)
 #endif
 
-__constant__ float c_albedo[8][3] = {
-    {0.55f, 0.50f, 0.40f}, {0.35f, 0.55f, 0.25f}, {0.60f, 0.60f, 0.62f}, {0.80f, 0.72f, 0.50f},
-    {0.30f, 0.30f, 0.32f}, {0.70f, 0.35f, 0.20f}, {0.90f, 0.90f, 0.95f}, {0.25f, 0.40f, 0.60f},
-};
-constexpr float kKa = 0.3f, kKd = 0.7f;
-constexpr uint32_t kSky = 0xFFEBB487u;  // r 135, g 180, b 235, a 255
+__constant__ float c_albedo[8][3] = HF_ALBEDO_TABLE;
+constexpr float kKa = kAmbient, kKd = kDiffuse;
+constexpr uint32_t kSky = kSkyColour;
 
 struct Ray {
     int32_t ox, oy, oz, dx, dy, dz;

@@ -169,3 +169,16 @@ def test_create_pairs_rejects_before_touching_the_gpu(hf):
         with pytest.raises(hf.HFError) as e:
             hf.hf_create_pairs(t)
         assert e.value.code == hf.HF_E_INVALID_ARG
+
+
+def test_scatter_footprint_agrees_with_the_input_helper(hf):
+    from synth.scatter import footprint_for
+
+    cams = list(synth.config_c1()["cams"]) + [
+        synth.camera_array([synth.pose_to_camera(50.0, 60.0, z, yaw, p, fov, 64, 40)])[0]
+        for z, yaw, p, fov in ((10.0, 0.0, 0.0, 90.0), (200.0, 33.0, -90.0, 75.0),
+                               (120.0, 250.0, -60.0, 60.0), (30.0, 100.0, 20.0, 80.0))]
+    for cam in cams:
+        a = np.array(hf.hf_scatter_footprint(cam))
+        b = np.array(footprint_for(cam))
+        assert np.allclose(a, b, rtol=1e-5, atol=1e-4), (a, b)

@@ -63,7 +63,7 @@ def test_footprint_warp_crowds_samples_near_the_camera():
     assert abs(col[0] - (-2.0 + 302.0 * (0.5 / 64) ** 2)) < 1e-3
     assert abs(col[-1] - (-2.0 + 302.0 * (63.5 / 64) ** 2)) < 1e-2
     u = (x - k["Of"][0]) * k["rh"][0] + (y - k["Of"][1]) * k["rh"][1]
-    half = np.maximum(3.0, np.abs(col) * 0.5)
+    half = 3.0 + np.abs(col) * 0.5
     assert np.allclose(np.abs(u[:, [0, 7]]).max(axis=1), half * (7 / 8), rtol=1e-4, atol=1e-3)
 
 
