@@ -299,6 +299,54 @@ int hf_scatter_footprint(const hf_camera *cam, float far_dist, hf_footprint *out
 int hf_render_scatter(hf_ctx *ctx, const hf_camera *cams, uint32_t n, const hf_footprint *fps,
                       const hf_outputs *outs, const hf_scatter_opts *opts);
 
+/* The paper's voxel-accelerated ray march, RayVoxel (Section 3), as a
+ * comparison renderer.  A conservative occupancy pyramid: level-0 voxel
+ * (i, j, k) covers cells [i vx, (i+1) vx) x [j vy, (j+1) vy) and heights
+ * [k vz, (k+1) vz] (closed) and is occupied when some of its cells is solid at
+ * some of its heights; each higher level is the union of eight children; every
+ * level is stored as Morton-coded 8 x 8 x 8 tiles of bits (tile (tx, ty, tz) at
+ * (tz TY + ty) TX + tx, 16 words per tile, voxel bit at the interleaving of
+ * the bits of x, y, z from the lowest).  The paper's publication grid (4,8,2)
+ * of its 2048 x 16384 level is vx 4, vy 8, vz 2 (18.29 MiB).  Traversal per
+ * pixel ray (float32 in a fixed order, no fused multiply-add): clip to the
+ * voxel box and the far distance, start at the top level, advance an empty
+ * voxel to its exit plane (climbing when the plane bounds the parent), open an
+ * occupied one, and sample an occupied leaf at `inner` midpoints of the ray's
+ * stretch in it; the first solid sample is the hit.  A feature thinner than
+ * the sample spacing can be missed (the paper's trade-off). */
+typedef struct {
+    uint32_t vx, vy, vz;  /* voxel extent in cells and height units (1..64, 1..64, 1..256) */
+    uint32_t levels;      /* pyramid levels (1..16); 0 = until the top level has at most 8
+                             voxels along every axis */
+} hf_voxel_desc;
+
+typedef struct {
+    uint32_t outer;     /* traversal steps per ray (<= 2^20); 0 = 1024 */
+    uint32_t inner;     /* samples per occupied leaf voxel (<= 4096); 0 = 4 */
+    float far_dist;     /* world units; 0 = 600 */
+    uint32_t flags;     /* HF_SYNC */
+    void *cuda_stream;  /* NULL = the context's stream */
+} hf_voxel_opts;
+
+/* Build (or rebuild with new extents) the context's voxel pyramid from its
+ * cells; later hf_edit and hf_rebuild calls keep it current (the edited
+ * columns' voxels at level 0, then the covering words of each level above).
+ * Synchronous.  Errors: HF_E_INVALID_ARG (null, extents or levels out of
+ * range), HF_E_OOM, HF_E_CUDA. */
+int hf_voxel_build(hf_ctx *ctx, const hf_voxel_desc *desc);
+
+/* Copy voxel level `level` to HOST memory (synchronous): with out == NULL,
+ * store its word count in *n_words; else *n_words must equal that count.
+ * Errors: HF_E_INVALID_ARG (no voxel pyramid, bad level or count), HF_E_CUDA. */
+int hf_read_voxels(hf_ctx *ctx, uint32_t level, uint32_t *out, size_t *n_words);
+
+/* RayVoxel-render n cameras: writes hit_cell, layer and depth (a miss: 0xFFFFFFFF,
+ * 255, +inf); face, rgba, shadow are not written.  Needs hf_voxel_build first.
+ * Ordering as hf_render.  Errors: as hf_render, and HF_E_INVALID_ARG without a
+ * voxel pyramid or with out-of-range options. */
+int hf_render_voxel(hf_ctx *ctx, const hf_camera *cams, uint32_t n, const hf_outputs *outs,
+                    const hf_voxel_opts *opts);
+
 /* The paper's own height-field ray march (Section 3.1), for comparison with
  * the exact cast: per pixel ray, clip the segment at the far distance and, for
  * a descending ray, at z = 0; take `steps` samples spaced uniformly over it

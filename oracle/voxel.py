@@ -24,6 +24,8 @@ Traversal, per pixel ray (float32; o = origin / 2^16, d = integer direction /
   repeat at most `outer` times:
     t_out = the least exit time of the current voxel over the axes
       (axis a: ((i_a + [d_a > 0]) * size_a - o_a) * (1 / d_a); +inf if d_a = 0)
+    (a voxel past the level's end, a missing child of the last parent of an
+    odd count, is empty)
     occupied and level > 0: go one level down, to the child the ray is in
       just after t: on the axis it last stepped across, the first child along
       its direction; on the other axes (all of them before the first step)
@@ -48,8 +50,11 @@ INF = f32(np.inf)
 # --------------------------------------------------------------- occupancy
 
 def level0(cells, vx, vy, vz):
-    """Dense bool [nz0, ny0, nx0] level-0 occupancy, straight from the definition
-    (vectorised over cells; one pass per voxel layer)."""
+    """Dense bool [nz0, ny0, nx0] level-0 occupancy, on whole arrays: a cell's
+    floor fills layers 0 .. floor(h0 / vz) (z0 = k vz <= h0), its slab layers
+    ceil(h1 / vz) - 1 .. floor(h2 / vz) (h1 <= (k+1) vz and k vz <= h2); a
+    voxel column takes the union over its cells (the floor part as a maximum,
+    the slab part through a difference array over the layers)."""
     c = np.asarray(cells, np.uint32)
     H, W = c.shape
     h0 = (c & 0xFF).astype(np.int64)
@@ -57,14 +62,20 @@ def level0(cells, vx, vy, vz):
     h2 = ((c >> 16) & 0xFF).astype(np.int64)
     slab = h1 > h0
     nx0, ny0, nz0 = -(-W // vx), -(-H // vy), -(-256 // vz)
-    occ = np.zeros((nz0, ny0, nx0), bool)
-    for k in range(nz0):
-        z0, z1 = k * vz, (k + 1) * vz
-        col = (z0 <= h0) | (slab & (h1 <= z1) & (z0 <= h2))
-        pad = np.zeros((ny0 * vy, nx0 * vx), bool)
-        pad[:H, :W] = col
-        occ[k] = pad.reshape(ny0, vy, nx0, vx).any(axis=(1, 3))
-    return occ
+    ys, xs = np.mgrid[0:H, 0:W]
+    col = (ys // vy) * nx0 + (xs // vx)  # voxel column of each cell
+    kf = np.full(ny0 * nx0, -1, np.int64)
+    np.maximum.at(kf, col.ravel(), np.minimum(h0 // vz, nz0 - 1).ravel())
+    diff = np.zeros((ny0 * nx0, nz0 + 1), np.int64)
+    ka = np.maximum(0, -(-h1 // vz) - 1)[slab]
+    kb = np.minimum(h2 // vz, nz0 - 1)[slab]
+    cs = col[slab]
+    keep = ka <= kb
+    np.add.at(diff, (cs[keep], ka[keep]), 1)
+    np.add.at(diff, (cs[keep], kb[keep] + 1), -1)
+    slab_occ = np.cumsum(diff[:, :nz0], axis=1) > 0
+    occ = slab_occ | (np.arange(nz0)[None, :] <= kf[:, None])
+    return np.ascontiguousarray(occ.T.reshape(nz0, ny0, nx0))
 
 
 def level0_loop(cells, vx, vy, vz):
@@ -114,11 +125,27 @@ def pack(level):
     nz, ny, nx = level.shape
     TX, TY, TZ = -(-nx // 8), -(-ny // 8), -(-nz // 8)
     words = np.zeros(TX * TY * TZ * 16, np.uint32)
-    z, y, x = np.nonzero(level)
+    z, y, x = (a.astype(np.int64) for a in np.nonzero(level))
     tile = ((z >> 3) * TY + (y >> 3)) * TX + (x >> 3)
-    m = np.array([morton3(a & 7, b & 7, c & 7) for a, b, c in zip(x, y, z)], np.int64) \
-        if len(x) else np.zeros(0, np.int64)
+    m = np.zeros(len(x), np.int64)
+    for b in range(3):  # morton3, on whole arrays
+        m |= ((x >> b) & 1) << (3 * b) | ((y >> b) & 1) << (3 * b + 1) | ((z >> b) & 1) << (3 * b + 2)
     np.bitwise_or.at(words, tile * 16 + (m >> 5), (np.uint32(1) << (m & 31).astype(np.uint32)))
+    return words
+
+
+def pack_loop(level):
+    """pack, one voxel at a time with morton3 (small levels; pins pack)."""
+    nz, ny, nx = level.shape
+    TX, TY, TZ = -(-nx // 8), -(-ny // 8), -(-nz // 8)
+    words = np.zeros(TX * TY * TZ * 16, np.uint32)
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                if level[z, y, x]:
+                    m = morton3(x & 7, y & 7, z & 7)
+                    t = ((z >> 3) * TY + (y >> 3)) * TX + (x >> 3)
+                    words[t * 16 + (m >> 5)] |= np.uint32(1 << (m & 31))
     return words
 
 
@@ -154,9 +181,14 @@ class Grid:
         self.top = levels - 1
 
     def occupied(self, l, ix, iy, iz):
+        """A voxel past the level's end (a missing child of the last parent
+        of an odd count) is empty."""
         nx = np.array([d[0] for d in self.dims])[l]
         ny = np.array([d[1] for d in self.dims])[l]
-        return self.flat[self.off[l] + (iz * ny + iy) * nx + ix]
+        nz = np.array([d[2] for d in self.dims])[l]
+        inside = (ix < nx) & (iy < ny) & (iz < nz)
+        k = self.off[l] + (np.minimum(iz, nz - 1) * ny + np.minimum(iy, ny - 1)) * nx + np.minimum(ix, nx - 1)
+        return inside & self.flat[k]
 
 
 def _setup(g, origin, dirs, far):
@@ -303,7 +335,8 @@ def trace_one(g, origin, direction, far=600.0, outer=4096, inner=4, visits=None)
             b = f32((idx[a] + (1 if d[a] > 0 else 0)) * (g.v[a] << l))
             tout.append((b - o[a]) * inv[a])
         t_out = min(min(tout[0], tout[1]), tout[2])
-        occ = bool(g.levels[l][idx[2], idx[1], idx[0]])
+        inside = idx[0] < g.dims[l][0] and idx[1] < g.dims[l][1] and idx[2] < g.dims[l][2]
+        occ = inside and bool(g.levels[l][idx[2], idx[1], idx[0]])
         if visits is not None:
             visits.append((l, idx[0], idx[1], idx[2], occ, float(t)))
         if occ and l > 0:

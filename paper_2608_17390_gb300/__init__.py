@@ -105,6 +105,17 @@ class hf_scatter_opts(ctypes.Structure):
                 ("sun", ctypes.c_int32 * 3), ("cuda_stream", ctypes.c_void_p)]
 
 
+class hf_voxel_desc(ctypes.Structure):
+    _fields_ = [("vx", ctypes.c_uint32), ("vy", ctypes.c_uint32), ("vz", ctypes.c_uint32),
+                ("levels", ctypes.c_uint32)]
+
+
+class hf_voxel_opts(ctypes.Structure):
+    _fields_ = [("outer", ctypes.c_uint32), ("inner", ctypes.c_uint32),
+                ("far_dist", ctypes.c_float), ("flags", ctypes.c_uint32),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
 class hf_info_t(ctypes.Structure):
     _fields_ = [("width", ctypes.c_uint32), ("height", ctypes.c_uint32),
                 ("levels", ctypes.c_uint32), ("render_slots", ctypes.c_uint32),
@@ -135,6 +146,9 @@ _SIGS = {
     "hf_render_march": ([_P, _P, _U32, _P, ctypes.POINTER(hf_march_opts)], ctypes.c_int),
     "hf_render_scatter": ([_P, _P, _U32, _P, _P, ctypes.POINTER(hf_scatter_opts)], ctypes.c_int),
     "hf_scatter_footprint": ([_P, ctypes.c_float, ctypes.POINTER(hf_footprint)], ctypes.c_int),
+    "hf_voxel_build": ([_P, ctypes.POINTER(hf_voxel_desc)], ctypes.c_int),
+    "hf_read_voxels": ([_P, _U32, _P, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "hf_render_voxel": ([_P, _P, _U32, _P, ctypes.POINTER(hf_voxel_opts)], ctypes.c_int),
     "hf_sync": ([_P], ctypes.c_int),
     "hf_destroy": ([_P], ctypes.c_int),
     "hf_camera_from_pose": ([ctypes.c_double] * 6 + [_U32, _U32, ctypes.POINTER(hf_camera)],
@@ -321,6 +335,38 @@ def hf_render_scatter(ctx, cams, outs, footprints=None, opts=None):
     _check(lib.hf_render_scatter(ctx, recs.ctypes.data if n else None, n,
                                  fp.ctypes.data if fp is not None else None, oarr, popts),
            "hf_render_scatter")
+
+
+def hf_voxel_build(ctx, vx=4, vy=8, vz=2, levels=0):
+    """Build the context's RayVoxel occupancy pyramid (include/hf.h)."""
+    d = hf_voxel_desc(vx, vy, vz, levels)
+    _check(lib.hf_voxel_build(ctx, ctypes.byref(d)), "hf_voxel_build")
+
+
+def hf_read_voxels(ctx, level):
+    """uint32 words of one voxel level (Morton-coded 8^3 tiles)."""
+    n = ctypes.c_size_t(0)
+    _check(lib.hf_read_voxels(ctx, level, None, ctypes.byref(n)), "hf_read_voxels")
+    out = np.empty(n.value, np.uint32)
+    _check(lib.hf_read_voxels(ctx, level, out.ctypes.data, ctypes.byref(n)), "hf_read_voxels")
+    return out
+
+
+def make_voxel_opts(outer=0, inner=0, far_dist=0.0, flags=0, stream=None):
+    return hf_voxel_opts(outer, inner, far_dist, flags, stream)
+
+
+def hf_render_voxel(ctx, cams, outs, opts=None):
+    """RayVoxel render (comparison method; see include/hf.h).  Writes hit_cell,
+    layer and depth of each output dict."""
+    recs = camera_records(cams)
+    n = len(recs)
+    if len(outs) != n:
+        raise ValueError("one output set per camera")
+    oarr = _outputs_array(outs)
+    popts = ctypes.byref(opts) if opts is not None else None
+    _check(lib.hf_render_voxel(ctx, recs.ctypes.data if n else None, n, oarr, popts),
+           "hf_render_voxel")
 
 
 def make_march_opts(steps=0, bisections=0, far_dist=0.0, tile_w=0, tile_h=0, flags=0,

@@ -68,6 +68,9 @@ struct hf_ctx {
     int occ[2][2] = {{0, 0}, {0, 0}};
     int occ_march = 0;
     bool pair = false;  // level 0 holds paired 2-byte texels (hf_create_pairs)
+    uint32_t *d_vox = nullptr;  // voxel occupancy pyramid (hf_voxel_build), or null
+    size_t vox_words = 0;
+    hf::VoxelDev vd{};
 };
 
 #define CK(call)                                   \
@@ -300,6 +303,7 @@ int hf_destroy(hf_ctx *c) {
     if (c->d_status) cudaFree(c->d_status);
     if (c->d_stats) cudaFree(c->d_stats);
     if (c->d_world) cudaFree(c->d_world);
+    if (c->d_vox) cudaFree(c->d_vox);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     (void)cudaGetLastError();
     delete c;
@@ -491,6 +495,9 @@ int hf_edit(hf_ctx *c, uint32_t x0, uint32_t y0, uint32_t w, uint32_t h, const u
     if (hf::pyramid_repair(c->d_world, c->wd, (int32_t)x0, (int32_t)y0, (int32_t)(x0 + w),
                            (int32_t)(y0 + h), c->stream))
         return HF_E_CUDA;
+    if (c->d_vox && hf::voxel_repair(c->wd, c->vd, (int32_t)x0, (int32_t)y0, (int32_t)(x0 + w),
+                                     (int32_t)(y0 + h), false, c->stream))
+        return HF_E_CUDA;
     CK(cudaEventRecord(c->edit_done, c->stream));
     return HF_OK;
 }
@@ -501,6 +508,11 @@ int hf_rebuild(hf_ctx *c) {
     for (auto &s : c->slots)
         if (s.pending) CK(cudaStreamWaitEvent(c->stream, s.done, 0));
     if (hf::pyramid_build(c->d_world, c->wd, c->stream)) return HF_E_CUDA;
+    if (c->d_vox) {
+        CK(cudaMemsetAsync(c->d_vox, 0, c->vox_words * 4, c->stream));
+        if (hf::voxel_repair(c->wd, c->vd, 0, 0, (int32_t)c->W, (int32_t)c->H, true, c->stream))
+            return HF_E_CUDA;
+    }
     CK(cudaEventRecord(c->edit_done, c->stream));
     return HF_OK;
 }
@@ -955,6 +967,97 @@ int hf_render_scatter(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_foo
                 fp.data(), (size_t)n * sizeof(hf_footprint));
     CK(cudaMemcpyAsync(s.d_scratch, s.h_staging, b.bytes, cudaMemcpyHostToDevice, b.stream));
     if (hf::launch_scatter(b.p, sp, n, b.stream)) return HF_E_CUDA;
+    return finish_batch(c, b, (o.flags & HF_SYNC) != 0);
+}
+
+int hf_voxel_build(hf_ctx *c, const hf_voxel_desc *d) {
+    if (!c || !d) return HF_E_INVALID_ARG;
+    if (d->vx < 1 || d->vy < 1 || d->vz < 1 || d->vx > 64 || d->vy > 64 || d->vz > 256 ||
+        d->levels > (uint32_t)hf::kVoxMaxLevels)
+        return HF_E_INVALID_ARG;
+    hf::VoxelDev v{};
+    v.vx = (int32_t)d->vx;
+    v.vy = (int32_t)d->vy;
+    v.vz = (int32_t)d->vz;
+    const int32_t n0[3] = {(int32_t)((c->W + d->vx - 1) / d->vx), (int32_t)((c->H + d->vy - 1) / d->vy),
+                           (int32_t)((256 + d->vz - 1) / d->vz)};
+    int32_t levels = (int32_t)d->levels;
+    if (levels == 0) {  // enough levels that the top one is at most 8 voxels along every axis
+        levels = 1;
+        while (levels < hf::kVoxMaxLevels &&
+               std::max({n0[0], n0[1], n0[2]}) > (8 << (levels - 1)))
+            ++levels;
+    }
+    v.levels = levels;
+    size_t off = 0;
+    for (int l = 0; l < levels; ++l) {
+        v.nx[l] = (n0[0] + (1 << l) - 1) >> l;
+        v.ny[l] = (n0[1] + (1 << l) - 1) >> l;
+        v.nz[l] = (n0[2] + (1 << l) - 1) >> l;
+        v.tx[l] = (v.nx[l] + 7) >> 3;
+        v.ty[l] = (v.ny[l] + 7) >> 3;
+        v.off[l] = (uint32_t)off;
+        off += (size_t)v.tx[l] * v.ty[l] * ((v.nz[l] + 7) >> 3) * 16;
+    }
+    CK(cudaSetDevice(c->device));
+    for (auto &s : c->slots)
+        if (s.pending) CK(cudaStreamWaitEvent(c->stream, s.done, 0));
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->d_vox) {
+        cudaFree(c->d_vox);
+        c->d_vox = nullptr;
+    }
+    if (cudaMalloc(&c->d_vox, off * 4) != cudaSuccess) {
+        (void)cudaGetLastError();
+        c->d_vox = nullptr;
+        return HF_E_OOM;
+    }
+    v.words = c->d_vox;
+    c->vd = v;
+    c->vox_words = off;
+    CK(cudaMemsetAsync(c->d_vox, 0, off * 4, c->stream));
+    if (hf::voxel_repair(c->wd, c->vd, 0, 0, (int32_t)c->W, (int32_t)c->H, true, c->stream))
+        return HF_E_CUDA;
+    CK(cudaEventRecord(c->edit_done, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return HF_OK;
+}
+
+int hf_read_voxels(hf_ctx *c, uint32_t level, uint32_t *out, size_t *n_words) {
+    if (!c || !n_words || !c->d_vox || level >= (uint32_t)c->vd.levels) return HF_E_INVALID_ARG;
+    const size_t end = level + 1 < (uint32_t)c->vd.levels ? c->vd.off[level + 1] : c->vox_words;
+    const size_t n = end - c->vd.off[level];
+    if (!out) {
+        *n_words = n;
+        return HF_OK;
+    }
+    if (*n_words != n) return HF_E_INVALID_ARG;
+    CK(cudaSetDevice(c->device));
+    CK(cudaMemcpyAsync(out, c->d_vox + c->vd.off[level], n * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return HF_OK;
+}
+
+int hf_render_voxel(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_outputs *outs,
+                    const hf_voxel_opts *opts) {
+    if (!c) return HF_E_INVALID_ARG;
+    if (n == 0) return HF_OK;
+    if (!cams || !outs || n > HF_MAX_CAMERAS || !c->d_vox) return HF_E_INVALID_ARG;
+    hf_voxel_opts o{};
+    if (opts) o = *opts;
+    hf::VoxelParams q;
+    q.outer = (int32_t)(o.outer ? o.outer : 1024);
+    q.inner = (int32_t)(o.inner ? o.inner : 4);
+    q.far_dist = o.far_dist != 0.0f ? o.far_dist : 600.0f;
+    if (o.outer > 1u << 20 || o.inner > 4096 || !(q.far_dist > 0.0f)) return HF_E_INVALID_ARG;
+    uint32_t maxpix = 0;
+    for (uint32_t i = 0; i < n; ++i) maxpix = std::max(maxpix, cams[i].w * cams[i].h);
+    Batch b;
+    int rc = prepare_batch(c, cams, n, outs, 8, 4, false, o.cuda_stream, b);
+    if (rc != HF_OK) return rc;
+    Slot &s = c->slots[b.slot];
+    CK(cudaMemcpyAsync(s.d_scratch, s.h_staging, b.bytes, cudaMemcpyHostToDevice, b.stream));
+    if (hf::launch_voxel_trace(b.p, c->vd, q, n, maxpix, b.stream)) return HF_E_CUDA;
     return finish_batch(c, b, (o.flags & HF_SYNC) != 0);
 }
 

@@ -155,6 +155,30 @@ struct ScatterParams {
 };
 int launch_scatter(const RenderParams &p, const ScatterParams &s, uint32_t n_cams, void *stream);
 
+// The voxel occupancy pyramid of the RayVoxel comparison renderer
+// (hf_voxel.cu): level l of nx x ny x nz voxels in Morton-coded 8^3 tiles of
+// tx x ty x tz tiles, 16 words each, starting at word off[l].
+constexpr int kVoxMaxLevels = 16;
+constexpr int kVoxMaxLayers = 256;  // nz0 = ceil(256 / vz), vz >= 1
+struct VoxelDev {
+    uint32_t *words;
+    uint32_t off[kVoxMaxLevels];
+    int32_t nx[kVoxMaxLevels], ny[kVoxMaxLevels], nz[kVoxMaxLevels];
+    int32_t tx[kVoxMaxLevels], ty[kVoxMaxLevels];
+    int32_t vx, vy, vz, levels;
+};
+struct VoxelParams {
+    int32_t outer;    // traversal steps allowed per ray
+    int32_t inner;    // samples per occupied leaf voxel
+    float far_dist;   // world units
+};
+// Recompute the voxels over cell rectangle [x0, x1) x [y0, y1), every level
+// (fresh: the words are zero, as after allocation).
+int voxel_repair(const WorldDev &w, const VoxelDev &v, int32_t x0, int32_t y0, int32_t x1,
+                 int32_t y1, bool fresh, void *stream);
+int launch_voxel_trace(const RenderParams &p, const VoxelDev &v, const VoxelParams &q,
+                       uint32_t n_cams, uint32_t max_pixels, void *stream);
+
 // Launch wrappers (hf_trace.cu)
 // The trace kernels are instantiated per level-0 storage; p.world.pair picks one.
 int launch_trace_batched(const RenderParams &p, bool shadows, bool stats, int blocks,

@@ -66,6 +66,9 @@ def test_morton_bits_and_tile_packing_by_hand():
     lv[0, 0, 0] = True   # tile 0, bit 0
     lv[3, 5, 6] = True   # tile 0, local (6, 5, 3): morton 6 + 40 + 192 = 238 -> word 7 bit 14
     w = voxel.pack(lv)
+    assert np.array_equal(w, voxel.pack_loop(lv))
+    rnd = np.random.default_rng(1).random((19, 23, 17)) < 0.3
+    assert np.array_equal(voxel.pack(rnd), voxel.pack_loop(rnd))
     assert w.size == 2 * 3 * 2 * 16
     want = np.zeros_like(w)
     want[11 * 16 + 0] |= 1 << 1
@@ -153,7 +156,7 @@ def test_close_to_the_exact_cast_with_fine_voxels_and_dense_samples():
 MUTANTS = [
     ("occupancy by intersection", ".any(axis=(1, 3, 5)))", ".all(axis=(1, 3, 5)))",
      "test_levels_are_unions_of_their_children"),
-    ("open floor interval", "col = (z0 <= h0) |", "col = (z0 < h0) |",
+    ("open floor interval", "np.minimum(h0 // vz, nz0 - 1)", "np.minimum((h0 - 1) // vz, nz0 - 1)",
      "test_level0_occupancy_equals_the_per_voxel_loop"),
     ("climb on the wrong parity", "up[m] = np.where(sgn > 0, ia % 2 == 0, ia % 2 == 1)",
      "up[m] = np.where(sgn > 0, ia % 2 == 1, ia % 2 == 0)",
