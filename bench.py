@@ -706,7 +706,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)  # about 1 s timed: several clock samples at 200 ms
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hf", choices=["hf", "reference"])
     ap.add_argument("--workload", default="c3",

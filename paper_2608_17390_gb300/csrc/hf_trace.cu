@@ -85,6 +85,16 @@ __device__ __forceinline__ uint32_t load_word(const WorldDev &w, int level, int3
     return __ldg(w.base + w.off[level] + (uint32_t)y * w.stride[level] + (uint32_t)x);
 }
 
+// Node-form word of level-0 cell (x, y) for the storage the kernel was
+// instantiated for (the choice is made at compile time).
+template <bool PAIR>
+__device__ __forceinline__ uint32_t level0_word(const WorldDev &w, int32_t x, int32_t y) {
+    if (PAIR)
+        return pair_node(__ldg(w.base + (uint32_t)y * ((uint32_t)w.W >> 1) + ((uint32_t)x >> 1)),
+                         (uint32_t)x & 1);
+    return load_word(w, 0, x, y);
+}
+
 // The two-interval test of one cell over [tin, tout] (tout finite).
 // Returns true and fills h on a hit.
 __device__ __forceinline__ bool leaf_test(const Ray &r, uint32_t word, int32_t tin_num,
@@ -200,7 +210,7 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const LevelDev *lvt
     if ((uint32_t)cx >= (uint32_t)w.W || (uint32_t)cy >= (uint32_t)w.H) return;
 
     if (adx == 0 && ady == 0) {
-        const uint32_t word = level0_node(w, cx, cy);
+        const uint32_t word = level0_word<PAIR>(w, cx, cy);
         if (STATS) cnt.cells++;
         if (vertical_test(r, word, h)) {
             h.cx = cx;
@@ -422,13 +432,15 @@ __device__ __forceinline__ void trace_pixel(const RenderParams &p, const LevelDe
 // exact from any start level (a ray climbs as it crosses parent boundaries);
 // the rule only saves descents through nodes around the camera that cannot
 // be empty.
+template <bool PAIR>
 __device__ __forceinline__ int primary_start(const RenderParams &p, const CamDev &c, int lane) {
     const WorldDev &w = p.world;
     const int32_t cx = c.o[0] >> kShift, cy = c.o[1] >> kShift;
     if ((uint32_t)cx >= (uint32_t)w.W || (uint32_t)cy >= (uint32_t)w.H) return p.mip_start;
     bool above = false;
     if (lane <= p.mip_start) {
-        const uint32_t word = lane ? load_word(w, lane, cx >> lane, cy >> lane) : level0_node(w, cx, cy);
+        const uint32_t word =
+            lane ? load_word(w, lane, cx >> lane, cy >> lane) : level0_word<PAIR>(w, cx, cy);
         const int32_t top = (word >> 16) & 0xFF;  // every level in node form
         above = c.o[2] > (top << kShift);
     }
@@ -447,7 +459,7 @@ __device__ __forceinline__ void trace_tile(const RenderParams &p, const LevelDev
     Counters cnt{0, 0}, scnt{0, 0};
     uint32_t nshadow = 0, nrays = 0;
     bool err = false;
-    const int start = primary_start(p, c, lane);
+    const int start = primary_start<PAIR>(p, c, lane);
     for (int i = lane; i < npix; i += 32) {
         const int32_t px = x0 + (i & ((1 << tw_log2) - 1));
         const int32_t py = y0 + (i >> tw_log2);
