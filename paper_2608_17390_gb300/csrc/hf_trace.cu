@@ -375,11 +375,16 @@ __device__ __forceinline__ void trace_pixel(const RenderParams &p, const LevelDe
     bool shadow_pass = false;
     for (;;) {
         Hit h;
-        if (!SHADOWS || !shadow_pass) {
-            trace_ray<STATS, PAIR>(p.world, lvt, r, start, p.mip_start, p.max_steps, h, cnt);
-        } else {
-            trace_ray<STATS, PAIR>(p.world, lvt, r, min(kShadowStart, p.shadow_mip), p.shadow_mip,
-                             p.max_steps, h, scnt);
+        // one call site: lanes in the primary and in the shadow pass run the
+        // same traversal code together
+        const bool sp = SHADOWS && shadow_pass;
+        Counters pc{0, 0};
+        trace_ray<STATS, PAIR>(p.world, lvt, r, sp ? min(kShadowStart, p.shadow_mip) : start,
+                               sp ? p.shadow_mip : p.mip_start, p.max_steps, h, pc);
+        if (STATS) {
+            Counters &dst = sp ? scnt : cnt;
+            dst.nodes += pc.nodes;
+            dst.cells += pc.cells;
         }
         if (h.face == kFaceError) err = true;
         if (SHADOWS && shadow_pass) {
