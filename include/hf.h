@@ -69,6 +69,12 @@ extern "C" {
 #define HF_NOGRAPH 16u /* launch directly instead of replaying a captured CUDA graph */
 #define HF_NOWAIT 32u /* return HF_E_BUSY instead of waiting for a free render slot */
 #define HF_SCATTER_RAW 128u /* hf_render_scatter: leave the packed words in hit_cell, no resolve */
+#define HF_HOST_STAGED 256u /* the output buffers are pinned HOST memory: the library renders the
+                               cameras in about 16 contiguous chunks into its own device staging
+                               (four buffers of the largest chunk, allocated on first use) and
+                               copies each finished chunk back on a copy stream while later
+                               chunks render (hf_render only; not with HF_HOST_OUTPUTS, HF_PLAIN
+                               or HF_NOWAIT) */
 #define HF_HOST_OUTPUTS 64u /* the output buffers are pinned HOST memory (cudaHostAlloc or
                                cudaHostRegister): the kernel writes the results there itself,
                                over the host link, with no separate copy (hf_render only) */
@@ -126,8 +132,9 @@ typedef struct {
 
 /* Per-camera output buffers, each w*h elements in row-major pixel order
  * (py*w + px): DEVICE memory, or pinned HOST memory with HF_HOST_OUTPUTS.
- * Caller-owned; they must stay allocated until the render has completed on
- * its stream.  A NULL member is not written. */
+ * (HF_HOST_STAGED: pinned HOST memory too).  Caller-owned; they must stay
+ * allocated until the render has completed on its stream.  A NULL member is
+ * not written. */
 typedef struct {
     uint32_t *hit_cell; /* y*W + x of the hit cell; 0xFFFFFFFF on a miss */
     uint8_t *layer;     /* 0 floor, 1 slab, 255 miss */
@@ -144,7 +151,7 @@ typedef struct {
                                 0 = flat cell-by-cell DDA; HF_MIP_AUTO = library default;
                                 larger values are clamped to the pyramid's top level */
     uint32_t flags;          /* HF_SHADOWS | HF_PLAIN | HF_SYNC | HF_STATS | HF_NOGRAPH | HF_NOWAIT
-                                | HF_HOST_OUTPUTS */
+                                | HF_HOST_OUTPUTS | HF_HOST_STAGED */
     uint32_t max_steps;      /* traversal iterations allowed per ray; 0 = default guard */
     int32_t sun[3];          /* direction toward the sun; all zero = (321060, -321060, 262144),
                                 elevation 30 deg, azimuth 135 deg; each |sun_i| < 2^21 */

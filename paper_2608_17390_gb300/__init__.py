@@ -42,6 +42,7 @@ HF_NOGRAPH = 16
 HF_NOWAIT = 32
 HF_HOST_OUTPUTS = 64
 HF_SCATTER_RAW = 128
+HF_HOST_STAGED = 256
 HF_MIP_AUTO = 0xFFFFFFFF
 HF_MAX_DIM = 16384
 HF_MAX_CAMERAS = 4096

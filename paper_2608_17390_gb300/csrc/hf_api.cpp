@@ -71,6 +71,13 @@ struct hf_ctx {
     uint32_t *d_vox = nullptr;  // voxel occupancy pyramid (hf_voxel_build), or null
     size_t vox_words = 0;
     hf::VoxelDev vd{};
+    // HF_HOST_STAGED: two device staging buffers the chunks render into, and the
+    // copy stream that streams each finished chunk to the caller's host buffers
+    char *d_hstage = nullptr;
+    size_t hstage_half = 0;  // bytes of one staging buffer
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t stage_ready[4] = {}, stage_free[4] = {};
+    bool stage_busy[4] = {};
 };
 
 #define CK(call)                                   \
@@ -304,6 +311,15 @@ int hf_destroy(hf_ctx *c) {
     if (c->d_stats) cudaFree(c->d_stats);
     if (c->d_world) cudaFree(c->d_world);
     if (c->d_vox) cudaFree(c->d_vox);
+    if (c->copy_stream) {
+        if (cudaStreamSynchronize(c->copy_stream) != cudaSuccess) rc = HF_E_CUDA;
+        cudaStreamDestroy(c->copy_stream);
+    }
+    for (int b = 0; b < 4; ++b) {
+        if (c->stage_ready[b]) cudaEventDestroy(c->stage_ready[b]);
+        if (c->stage_free[b]) cudaEventDestroy(c->stage_free[b]);
+    }
+    if (c->d_hstage) cudaFree(c->d_hstage);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     (void)cudaGetLastError();
     delete c;
@@ -779,6 +795,164 @@ static int finish_batch(hf_ctx *c, Batch &b, bool sync) {
     return HF_OK;
 }
 
+// HF_HOST_STAGED: render the cameras in about kStageChunks contiguous chunks of
+// similar pixel counts into a ring of kBuffers device staging buffers, and
+// stream each finished chunk to the caller's pinned host buffers on the copy
+// stream while later chunks render.  The render stream waits for the last
+// copies.
+static int render_host_staged(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_outputs *outs,
+                              const hf_render_opts &o) {
+#ifndef HF_STAGE_CHUNKS
+#define HF_STAGE_CHUNKS 16  // measured: 4 / 8 / 16 / 32 chunks
+#endif
+#ifndef HF_STAGE_BUFFERS
+#define HF_STAGE_BUFFERS 4  // measured: 2 / 3 / 4 buffers
+#endif
+    constexpr uint32_t kStageChunks = HF_STAGE_CHUNKS;
+    constexpr int kBuffers = HF_STAGE_BUFFERS;
+    constexpr size_t kAlign = 256;
+    const bool shadows = (o.flags & HF_SHADOWS) != 0;
+    // the fields to move, with their element sizes
+    auto field_bytes = [&](const hf_outputs &u, int f) -> size_t {
+        switch (f) {
+            case 0: return u.hit_cell ? 4 : 0;
+            case 1: return u.layer ? 1 : 0;
+            case 2: return u.face ? 1 : 0;
+            case 3: return u.depth ? 4 : 0;
+            case 4: return u.rgba ? 4 : 0;
+            default: return (u.shadow && shadows) ? 1 : 0;
+        }
+    };
+    auto field_ptr = [](const hf_outputs &u, int f) -> void * {
+        switch (f) {
+            case 0: return u.hit_cell;
+            case 1: return u.layer;
+            case 2: return u.face;
+            case 3: return u.depth;
+            case 4: return u.rgba;
+            default: return u.shadow;
+        }
+    };
+    uint64_t total_px = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        if (hf_validate_camera(c->W, c->H, &cams[i]) != HF_OK) return HF_E_INVALID_ARG;
+        total_px += (uint64_t)cams[i].w * cams[i].h;
+        for (int f = 0; f < 6; ++f) {
+            void *ptr = field_ptr(outs[i], f);
+            if (!ptr) continue;
+            cudaPointerAttributes a;
+            if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+                (void)cudaGetLastError();
+                return HF_E_INVALID_ARG;
+            }
+            if (a.type != cudaMemoryTypeHost) return HF_E_INVALID_ARG;  // pinned host memory only
+        }
+    }
+    // chunks: contiguous cameras, about total / kStageChunks pixels each
+    std::vector<uint32_t> first;
+    {
+        const uint64_t target = (total_px + kStageChunks - 1) / kStageChunks;
+        uint64_t acc = 0;
+        first.push_back(0);
+        for (uint32_t i = 0; i < n; ++i) {
+            acc += (uint64_t)cams[i].w * cams[i].h;
+            if (acc >= target && i + 1 < n) {
+                first.push_back(i + 1);
+                acc = 0;
+            }
+        }
+        first.push_back(n);
+    }
+    auto cam_stage_bytes = [&](uint32_t i) {
+        size_t b = 0;
+        for (int f = 0; f < 6; ++f) {
+            const size_t fb = field_bytes(outs[i], f) * cams[i].w * cams[i].h;
+            b += (fb + kAlign - 1) & ~(kAlign - 1);
+        }
+        return b;
+    };
+    size_t need = 0;
+    for (size_t k = 0; k + 1 < first.size(); ++k) {
+        size_t b = 0;
+        for (uint32_t i = first[k]; i < first[k + 1]; ++i) b += cam_stage_bytes(i);
+        need = std::max(need, b);
+    }
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = o.cuda_stream ? (cudaStream_t)o.cuda_stream : c->stream;
+    if (!c->copy_stream) {
+        CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        for (int b = 0; b < 4; ++b) {
+            CK(cudaEventCreateWithFlags(&c->stage_ready[b], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&c->stage_free[b], cudaEventDisableTiming));
+        }
+    }
+    if (need > c->hstage_half) {  // grow: nothing may still use the old buffers
+        CK(cudaStreamSynchronize(c->copy_stream));
+        for (int b = 0; b < 4; ++b) c->stage_busy[b] = false;
+        sync_slots(c);
+        if (c->d_hstage) cudaFree(c->d_hstage);
+        c->d_hstage = nullptr;
+        c->hstage_half = 0;
+        const size_t half = (need + (1u << 20) - 1) & ~(size_t)((1u << 20) - 1);
+        if (cudaMalloc(&c->d_hstage, kBuffers * half) != cudaSuccess) {
+            (void)cudaGetLastError();
+            c->d_hstage = nullptr;
+            return HF_E_OOM;
+        }
+        c->hstage_half = half;
+    }
+    hf_render_opts inner = o;
+    inner.flags &= ~(HF_HOST_STAGED | HF_HOST_OUTPUTS | HF_SYNC);
+    inner.cuda_stream = s;
+    std::vector<hf_outputs> dev;
+    for (size_t k = 0; k + 1 < first.size(); ++k) {
+        const int b = (int)(k % kBuffers);
+        if (c->stage_busy[b]) CK(cudaStreamWaitEvent(s, c->stage_free[b], 0));
+        char *base = c->d_hstage + b * c->hstage_half;
+        dev.assign(first[k + 1] - first[k], hf_outputs{});
+        size_t off = 0;
+        for (uint32_t i = first[k]; i < first[k + 1]; ++i) {
+            hf_outputs &d = dev[i - first[k]];
+            void *slots[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+            for (int f = 0; f < 6; ++f) {
+                const size_t fb = field_bytes(outs[i], f) * cams[i].w * cams[i].h;
+                if (!fb) continue;
+                slots[f] = base + off;
+                off += (fb + kAlign - 1) & ~(kAlign - 1);
+            }
+            d.hit_cell = (uint32_t *)slots[0];
+            d.layer = (uint8_t *)slots[1];
+            d.face = (uint8_t *)slots[2];
+            d.depth = (float *)slots[3];
+            d.rgba = (uint32_t *)slots[4];
+            d.shadow = (uint8_t *)slots[5];
+        }
+        const int rc = hf_render(c, cams + first[k], first[k + 1] - first[k], dev.data(), &inner);
+        if (rc != HF_OK) return rc;
+        CK(cudaEventRecord(c->stage_ready[b], s));
+        CK(cudaStreamWaitEvent(c->copy_stream, c->stage_ready[b], 0));
+        for (uint32_t i = first[k]; i < first[k + 1]; ++i) {
+            const hf_outputs &d = dev[i - first[k]];
+            const void *src[6] = {d.hit_cell, d.layer, d.face, d.depth, d.rgba, d.shadow};
+            for (int f = 0; f < 6; ++f) {
+                const size_t fb = field_bytes(outs[i], f) * cams[i].w * cams[i].h;
+                if (fb)
+                    CK(cudaMemcpyAsync(field_ptr(outs[i], f), src[f], fb, cudaMemcpyDeviceToHost,
+                                       c->copy_stream));
+            }
+        }
+        CK(cudaEventRecord(c->stage_free[b], c->copy_stream));
+        c->stage_busy[b] = true;
+    }
+    for (int b = 0; b < kBuffers; ++b)
+        if (c->stage_busy[b]) CK(cudaStreamWaitEvent(s, c->stage_free[b], 0));
+    if (o.flags & HF_SYNC) {
+        CK(cudaStreamSynchronize(s));
+        return read_status(c);
+    }
+    return HF_OK;
+}
+
 int hf_render(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_outputs *outs,
               const hf_render_opts *opts) {
     if (!c) return HF_E_INVALID_ARG;
@@ -787,6 +961,10 @@ int hf_render(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_outputs *ou
     hf_render_opts o{};
     if (opts) o = *opts;
     else o.mip_start = HF_MIP_AUTO;
+    if (o.flags & HF_HOST_STAGED) {
+        if (o.flags & (HF_HOST_OUTPUTS | HF_PLAIN | HF_NOWAIT)) return HF_E_INVALID_ARG;
+        return render_host_staged(c, cams, n, outs, o);
+    }
     const uint32_t tw = o.tile_w ? o.tile_w : 8, th = o.tile_h ? o.tile_h : 4;
     int32_t sun[3] = {o.sun[0], o.sun[1], o.sun[2]};
     if (sun[0] == 0 && sun[1] == 0 && sun[2] == 0)

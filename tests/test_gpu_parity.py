@@ -550,3 +550,35 @@ def test_host_outputs_equal_device_outputs(hf, c1):
         hf.hf_sync(ctx)
     finally:
         hf.hf_destroy(ctx)
+
+
+def test_host_staged_outputs_equal_device_outputs(hf, c1):
+    """HF_HOST_STAGED: the library renders chunks into its own staging and
+    copies each back while the next renders; the host buffers equal a device
+    render bit for bit, for one camera and for a multi-chunk batch with some
+    fields absent; pageable memory and conflicting flags are refused."""
+    import torch
+
+    for cells, cams, fields, sh in (
+            (c1["cells"], c1["cams"], ("hit_cell", "layer", "face", "depth", "rgba", "shadow"), True),
+            (synth.config_c3(scale=8)["cells"], synth.config_c3(scale=8)["cams"],
+             ("hit_cell", "depth", "rgba"), False)):
+        ctx = _ctx(hf, cells)
+        try:
+            flags = hf.HF_SHADOWS if sh else 0
+            dev = gpu_render(hf, ctx, cams, shadows=sh, opts=hf.make_opts(flags=flags), fields=fields)
+            for rep in range(2):  # the second call reuses the staging buffers
+                host = hf.alloc_outputs(cams, device="pinned", shadows=sh, fields=fields)
+                hf.hf_render(ctx, cams, host, hf.make_opts(flags=flags | hf.HF_HOST_STAGED | hf.HF_SYNC))
+                for i in range(len(cams)):
+                    for k, t in host[i].items():
+                        assert (t.numpy() == dev[i][k].view(t.numpy().dtype)).all(), (rep, i, k)
+            pageable = [{k: torch.empty(v.shape, dtype=v.dtype) for k, v in o.items()} for o in host]
+            with pytest.raises(hf.HFError):
+                hf.hf_render(ctx, cams, pageable, hf.make_opts(flags=flags | hf.HF_HOST_STAGED))
+            for bad in (hf.HF_HOST_OUTPUTS, hf.HF_PLAIN, hf.HF_NOWAIT):
+                with pytest.raises(hf.HFError):
+                    hf.hf_render(ctx, cams, host, hf.make_opts(flags=flags | hf.HF_HOST_STAGED | bad))
+            hf.hf_sync(ctx)
+        finally:
+            hf.hf_destroy(ctx)
