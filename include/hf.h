@@ -63,7 +63,9 @@ extern "C" {
 
 /* hf_render_opts.flags */
 #define HF_SHADOWS 1u /* trace one shadow ray per hit toward the sun */
-#define HF_PLAIN 2u   /* one non-persistent launch per camera instead of one batched launch */
+#define HF_PLAIN 2u   /* one non-persistent launch per camera instead of one batched launch
+                         (always so for a single camera, unless HF_NOGRAPH asks for the
+                         persistent kernel) */
 #define HF_SYNC 4u    /* wait for the render and return its status (HF_E_STEP_LIMIT) */
 #define HF_STATS 8u   /* count node and cell fetches (read back with hf_stats) */
 #define HF_NOGRAPH 16u /* launch directly instead of replaying a captured CUDA graph */

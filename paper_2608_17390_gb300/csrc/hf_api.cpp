@@ -993,7 +993,9 @@ int hf_render(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_outputs *ou
         p.sun[i] = sun[i];
         p.sun_n[i] = (float)(sun[i] / sn);
     }
-    if (o.flags & HF_PLAIN) {
+    // one camera: the plain launch (its grid covers the camera's tiles) spares
+    // the persistent kernel's shared tile counter, which small tiles contend on
+    if ((o.flags & HF_PLAIN) || (n == 1 && !(o.flags & HF_NOGRAPH))) {
         CK(cudaMemcpyAsync(s.d_scratch, s.h_staging, b.bytes, cudaMemcpyHostToDevice, b.stream));
         for (uint32_t i = 0; i < n; ++i)
             if (hf::launch_trace_plain(p, shadows, stats, i, b.tiles[i], b.stream)) return HF_E_CUDA;
