@@ -104,23 +104,17 @@ def _alu_roofline(workload, rays, render_ms, tile, mip, sm_count, sm_mhz):
             "peak_source": "%d SMs x 4 schedulers x 1 instr/cycle x %.0f MHz" % (sm_count, sm_mhz)}
 
 
-def _profiled_traffic(workload, rays, scale):
+def _profiled_traffic(workload, rays, tile, mip):
     """DRAM bytes (read + write) per launch of the trace kernel, from the
     committed ncu summary of this workload: its measured bytes per ray times
     the rays of one launch here.  None when there is no summary, or when the
-    kernel source changed since the counters were taken."""
-    path = os.path.join(ROOT, "profiles", "trace_batched_%s.md" % workload)
-    if not os.path.exists(path):
-        return None
-    fields = {}
-    for line in open(path):
-        if ":" in line and line.startswith("- "):
-            k, v = line[2:].split(":", 1)
-            fields[k.strip()] = v.strip().strip("`")
-    if fields.get("kernel_source_sha256") != trace_source_hash():
+    kernel source or the launch configuration changed since the counters were
+    taken."""
+    f = _profile_fields(workload)
+    if not f or f.get("launch_tile") != tile or f.get("launch_mip_start") != str(mip):
         return None
     try:
-        return float(fields["dram_bytes_per_ray"]) * rays
+        return float(f["dram_bytes_per_ray"]) * rays
     except (KeyError, ValueError):
         return None
 
@@ -467,7 +461,7 @@ def run_hf(args):
     alg_bytes = fetch_b + out_b
     r_ms = float(np.mean(render_ms))
     achieved = alg_bytes / (r_ms / 1e3) / 1e9
-    traffic = _profiled_traffic(args.workload, rays, args.scale)
+    traffic = _profiled_traffic(args.workload, rays, "%dx%d" % (tile_w, tile_h), mip_start)
     line = {
         "metric": "primary rays/s (batched, exact two-interval height-field ray cast)",
         "value": value, "unit": "primary rays/s", "n_gpus": ws, "steps": args.steps,

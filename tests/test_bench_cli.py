@@ -40,17 +40,22 @@ def test_reference_arm_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
 
 
-def test_traffic_lookup_tracks_the_kernel_source():
+def test_traffic_lookup_tracks_the_kernel_source_and_launch():
     import bench
 
-    t = bench._profiled_traffic("c3", 1000, 1)
+    f = bench._profile_fields("c3")
     path = os.path.join(ROOT, "profiles", "trace_batched_c3.md")
     text = open(path).read()
-    if bench.trace_source_hash() in text:
-        assert t is not None and t > 0
-    else:
-        assert t is None
-    assert bench._profiled_traffic("no_such_workload", 1000, 1) is None
+    if bench.trace_source_hash() not in text:
+        assert f is None and bench._profiled_traffic("c3", 1000, "8x16", 5) is None
+        return
+    tile, mip = f["launch_tile"], int(f["launch_mip_start"])
+    t = bench._profiled_traffic("c3", 1000, tile, mip)
+    assert t is not None and t == pytest.approx(1000 * float(f["dram_bytes_per_ray"]))
+    other = "4x8" if tile != "4x8" else "8x4"
+    assert bench._profiled_traffic("c3", 1000, other, mip) is None
+    assert bench._profiled_traffic("c3", 1000, tile, mip + 1) is None
+    assert bench._profiled_traffic("no_such_workload", 1000, tile, mip) is None
 
 
 def test_alu_roofline_only_for_the_profiled_launch():
