@@ -85,38 +85,48 @@ def _profile_fields(workload):
     return fields
 
 
+def _profiled(workload, key, tile, mip):
+    """One per-launch figure from the committed ncu summary of this workload,
+    for the launch configuration (tile, mip start) given: the summary's main
+    capture when its configuration is this one, else a `key@tile/mip` line
+    taken for another configuration.  None when there is none, or when the
+    kernel source changed since the counters were taken."""
+    f = _profile_fields(workload)
+    if not f:
+        return None
+    if f.get("launch_tile") == tile and f.get("launch_mip_start") == str(mip) and key in f:
+        v = f[key]
+    else:
+        v = f.get("%s@%s/%s" % (key, tile, mip))
+    try:
+        return float(v) if v is not None else None
+    except ValueError:
+        return None
+
+
 def _alu_roofline(workload, rays, render_ms, tile, mip, sm_count, sm_mhz):
     """Instruction-issue roofline of the trace kernel: warp instructions per
     primary ray (ncu, full-size launch of the same source and launch
     configuration) times this launch's rays, over the live render time,
     against SMs x 4 schedulers x 1 instruction/cycle x the SM clock."""
-    f = _profile_fields(workload)
-    if not f or f.get("launch_tile") != tile or f.get("launch_mip_start") != str(mip):
-        return None
-    try:
-        per_ray = float(f["warp_instructions_per_primary_ray"])
-    except (KeyError, ValueError):
+    per_ray = _profiled(workload, "warp_instructions_per_primary_ray", tile, mip)
+    if per_ray is None:
         return None
     achieved = per_ray * rays / (render_ms / 1e3) / 1e12
     peak = sm_count * 4 * sm_mhz * 1e6 / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T warp-instr/s",
-            "frac": achieved / peak,
+            "frac": achieved / peak, "warp_instructions_per_primary_ray": per_ray,
             "peak_source": "%d SMs x 4 schedulers x 1 instr/cycle x %.0f MHz" % (sm_count, sm_mhz)}
 
 
 def _profiled_traffic(workload, rays, tile, mip):
     """DRAM bytes (read + write) per launch of the trace kernel, from the
-    committed ncu summary of this workload: its measured bytes per ray times
-    the rays of one launch here.  None when there is no summary, or when the
-    kernel source or the launch configuration changed since the counters were
-    taken."""
-    f = _profile_fields(workload)
-    if not f or f.get("launch_tile") != tile or f.get("launch_mip_start") != str(mip):
-        return None
-    try:
-        return float(f["dram_bytes_per_ray"]) * rays
-    except (KeyError, ValueError):
-        return None
+    committed ncu summary of this workload: its measured bytes per ray for
+    this launch configuration times the rays of one launch here.  None when
+    there is no such figure, or when the kernel source changed since the
+    counters were taken."""
+    per_ray = _profiled(workload, "dram_bytes_per_ray", tile, mip)
+    return None if per_ray is None else per_ray * rays
 
 
 # ------------------------------------------------------------------ workloads

@@ -54,8 +54,12 @@ def test_traffic_lookup_tracks_the_kernel_source_and_launch():
     assert t is not None and t == pytest.approx(1000 * float(f["dram_bytes_per_ray"]))
     other = "4x8" if tile != "4x8" else "8x4"
     assert bench._profiled_traffic("c3", 1000, other, mip) is None
-    assert bench._profiled_traffic("c3", 1000, tile, mip + 1) is None
+    assert bench._profiled_traffic("c3", 1000, tile, 2) is None
     assert bench._profiled_traffic("no_such_workload", 1000, tile, mip) is None
+    for key, v in f.items():  # figures taken for other launch configurations
+        if key.startswith("dram_bytes_per_ray@"):
+            t2, m2 = key.split("@")[1].split("/")
+            assert bench._profiled_traffic("c3", 1000, t2, int(m2)) == pytest.approx(1000 * float(v))
 
 
 def test_alu_roofline_only_for_the_profiled_launch():
@@ -71,4 +75,9 @@ def test_alu_roofline_only_for_the_profiled_launch():
     assert r["peak"] == pytest.approx(152 * 4 * 2070e6 / 1e12)
     other = "4x8" if tile != "4x8" else "8x4"
     assert bench._alu_roofline("c3", 188006400, 30.0, other, mip, 152, 2070.0) is None
-    assert bench._alu_roofline("c3", 188006400, 30.0, tile, mip + 1, 152, 2070.0) is None
+    assert bench._alu_roofline("c3", 188006400, 30.0, tile, 2, 152, 2070.0) is None
+    for key, v in f.items():
+        if key.startswith("warp_instructions_per_primary_ray@"):
+            t2, m2 = key.split("@")[1].split("/")
+            r2 = bench._alu_roofline("c3", 188006400, 30.0, t2, int(m2), 152, 2070.0)
+            assert r2["warp_instructions_per_primary_ray"] == pytest.approx(float(v))
