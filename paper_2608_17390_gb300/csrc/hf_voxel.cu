@@ -44,8 +44,39 @@ __device__ __forceinline__ void vox_addr(const VoxelDev &v, int l, uint32_t x, u
     bit = m & 31;
 }
 
-__device__ __forceinline__ int32_t vox_dim(const VoxelDev &v, int axis, int l) {
-    return axis == 0 ? v.nx[l] : (axis == 1 ? v.ny[l] : v.nz[l]);
+// One level of the pyramid as the traversal reads it: a per-block shared
+// table, so lanes at different levels read it in one shared-memory access
+// (kernel parameters indexed by a per-lane level would serialise).
+struct __align__(16) VoxLevel {
+    uint32_t off;
+    int32_t tx, ty, pad0;
+    int32_t n[3], pad1;
+};
+
+__device__ __forceinline__ bool vox_occupied(const VoxelDev &v, const VoxLevel &lv, uint32_t x,
+                                             uint32_t y, uint32_t z) {
+    const uint32_t tile = ((z >> 3) * (uint32_t)lv.ty + (y >> 3)) * (uint32_t)lv.tx + (x >> 3);
+    const uint32_t m = morton3(x & 7, y & 7, z & 7);
+    return (__ldg(v.words + lv.off + tile * 16 + (m >> 5)) >> (m & 31)) & 1u;
+}
+
+// leaf sample fractions (s + 0.5) / inner held in shared memory up to this count
+constexpr int kVoxFracTable = 64;
+
+// log2 of a power-of-two voxel extent, else -1
+__host__ __device__ __forceinline__ int32_t pow2_log2(int32_t v) {
+    if (v <= 0 || (v & (v - 1))) return -1;
+    int32_t e = 0;
+    while ((1 << e) < v) ++e;
+    return e;
+}
+
+// The correctly rounded quotient pk / (vs 2^l).  For a power-of-two extent
+// (vs = 2^e) it is the correctly rounded product pk 2^-(e+l): both round the
+// same real number, and 2^-(e+l) (at least 2^-21) is an exact float.
+__device__ __forceinline__ float vox_quot(float pk, int32_t vs, int32_t vs_log2, int l) {
+    if (vs_log2 >= 0) return __fmul_rn(pk, __int_as_float((127 - vs_log2 - l) << 23));
+    return __fdiv_rn(pk, (float)(vs << l));
 }
 
 __device__ __forceinline__ bool vox_occupied(const VoxelDev &v, int l, uint32_t x, uint32_t y,
@@ -133,6 +164,15 @@ __global__ void k_vox_up(const VoxelDev v, int l, int32_t ti0, int32_t tj0, int3
 
 __global__ void __launch_bounds__(kVoxThreads) k_vox_trace(const RenderParams p, const VoxelDev v,
                                                            const VoxelParams q) {
+    __shared__ VoxLevel s_lv[kVoxMaxLevels];
+    __shared__ float s_frac[kVoxFracTable];
+    if (threadIdx.x < (unsigned)v.levels) {
+        const int l = threadIdx.x;
+        s_lv[l] = VoxLevel{v.off[l], v.tx[l], v.ty[l], 0, {v.nx[l], v.ny[l], v.nz[l]}, 0};
+    }
+    if (threadIdx.x < (unsigned)min(q.inner, kVoxFracTable))
+        s_frac[threadIdx.x] = __fdiv_rn(__fadd_rn((float)threadIdx.x, 0.5f), (float)q.inner);
+    __syncthreads();
     const CamDev &c = p.cams[blockIdx.y];
     const uint32_t pix = blockIdx.x * blockDim.x + threadIdx.x;
     if (pix >= c.w * c.h) return;
@@ -141,6 +181,7 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_trace(const RenderParams p,
     const float inv_s = 1.0f / 65536.0f;
     float o[3], d[3], inv[3], box[3];
     int32_t vs[3] = {v.vx, v.vy, v.vz};
+    const int32_t ve[3] = {pow2_log2(v.vx), pow2_log2(v.vy), pow2_log2(v.vz)};
     for (int k = 0; k < 3; ++k) {
         o[k] = __fmul_rn(__int2float_rn(c.o[k]), inv_s);
         d[k] = __fmul_rn(__int2float_rn(c.F[k] + a * c.R[k] + b * c.U[k]), inv_s);
@@ -175,8 +216,8 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_trace(const RenderParams p,
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const float pk = __fadd_rn(o[k], __fmul_rn(d[k], t));
-            const float cf = floorf(__fdiv_rn(pk, (float)(vs[k] << l)));
-            idx[k] = (int32_t)fminf(fmaxf(cf, 0.0f), (float)(vox_dim(v, k, l) - 1));
+            const float cf = floorf(vox_quot(pk, vs[k], ve[k], l));
+            idx[k] = (int32_t)fminf(fmaxf(cf, 0.0f), (float)(s_lv[l].n[k] - 1));
         }
         for (int step = 0; step < q.outer; ++step) {
             float tk[3];
@@ -191,8 +232,9 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_trace(const RenderParams p,
             }
             const float t_out = fminf(fminf(tk[0], tk[1]), tk[2]);
             // a child past the level's end (the last parent of an odd count) is empty
-            const bool occ = idx[0] < v.nx[l] && idx[1] < v.ny[l] && idx[2] < v.nz[l] &&
-                             vox_occupied(v, l, idx[0], idx[1], idx[2]);
+            const VoxLevel &lv = s_lv[l];
+            const bool occ = idx[0] < lv.n[0] && idx[1] < lv.n[1] && idx[2] < lv.n[2] &&
+                             vox_occupied(v, lv, idx[0], idx[1], idx[2]);
             if (occ && l > 0) {
                 --l;
 #pragma unroll
@@ -201,7 +243,7 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_trace(const RenderParams p,
                         idx[k] = 2 * idx[k] + (d[k] < 0.0f ? 1 : 0);
                     } else {
                         const float pk = __fadd_rn(o[k], __fmul_rn(d[k], t));
-                        const float cf = floorf(__fdiv_rn(pk, (float)(vs[k] << l)));
+                        const float cf = floorf(vox_quot(pk, vs[k], ve[k], l));
                         idx[k] = (int32_t)fminf(fmaxf(cf, (float)(2 * idx[k])), (float)(2 * idx[k] + 1));
                     }
                 }
@@ -211,7 +253,9 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_trace(const RenderParams p,
                 const float span = __fsub_rn(fminf(t_out, t1), t);
                 bool found = false;
                 for (int s = 0; s < q.inner && !found; ++s) {
-                    const float frac = __fdiv_rn(__fadd_rn((float)s, 0.5f), (float)q.inner);
+                    const float frac = s < kVoxFracTable
+                                           ? s_frac[s]
+                                           : __fdiv_rn(__fadd_rn((float)s, 0.5f), (float)q.inner);
                     const float ts = __fadd_rn(t, __fmul_rn(span, frac));
                     const float x = __fadd_rn(o[0], __fmul_rn(d[0], ts));
                     const float y = __fadd_rn(o[1], __fmul_rn(d[1], ts));
@@ -243,7 +287,7 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_trace(const RenderParams p,
             else ni = (idx[2] += sg);
             t = t_out;
             ent = ax;
-            if (ni < 0 || ni >= vox_dim(v, ax, l)) break;
+            if (ni < 0 || ni >= lv.n[ax]) break;
             if (l < v.levels - 1 && ((ni & 1) == (sg > 0 ? 0 : 1))) {
                 ++l;
                 idx[0] >>= 1;
