@@ -71,15 +71,35 @@ __device__ __forceinline__ float dot3(float ax, float ay, float az, float bx, fl
     return __fadd_rn(__fadd_rn(__fmul_rn(ax, bx), __fmul_rn(ay, by)), __fmul_rn(az, bz));
 }
 
+// The parts of a point's view-space products that do not depend on its
+// height: for v = (vx, vy, vz), dot3(v, a) = (vx ax + vy ay) + vz az, and the
+// bracket is the same for every point of one column.
+struct ColumnPartials {
+    float vx, vy, pf, pr, pu, pd;
+};
+
+__device__ __forceinline__ ColumnPartials column_partials(const ScatterCam &k, float x, float y) {
+    ColumnPartials c;
+    c.vx = __fsub_rn(x, k.ox);
+    c.vy = __fsub_rn(y, k.oy);
+    c.pf = __fadd_rn(__fmul_rn(c.vx, k.Fx), __fmul_rn(c.vy, k.Fy));
+    c.pr = __fadd_rn(__fmul_rn(c.vx, k.Rx), __fmul_rn(c.vy, k.Ry));
+    c.pu = __fadd_rn(__fmul_rn(c.vx, k.Ux), __fmul_rn(c.vy, k.Uy));
+    c.pd = __fadd_rn(__fmul_rn(c.vx, c.vx), __fmul_rn(c.vy, c.vy));
+    return c;
+}
+
 // Packed depth word of a point without its type, or false when the point is
-// behind the camera or outside the image.
+// behind the camera or outside the image.  The same operations, in the same
+// order, as dot3 over the full vectors.
 __device__ __forceinline__ bool project(const ScatterCam &k, const CamDev &c, float qscale,
-                                        float x, float y, float z, uint32_t &pix, uint32_t &q) {
-    const float vx = __fsub_rn(x, k.ox), vy = __fsub_rn(y, k.oy), vz = __fsub_rn(z, k.oz);
-    const float vf = dot3(vx, vy, vz, k.Fx, k.Fy, k.Fz);
+                                        const ColumnPartials &cp, float z, uint32_t &pix,
+                                        uint32_t &q) {
+    const float vz = __fsub_rn(z, k.oz);
+    const float vf = __fadd_rn(cp.pf, __fmul_rn(vz, k.Fz));
     if (!(vf > 0.0f)) return false;
-    const float vr = dot3(vx, vy, vz, k.Rx, k.Ry, k.Rz);
-    const float vu = dot3(vx, vy, vz, k.Ux, k.Uy, k.Uz);
+    const float vr = __fadd_rn(cp.pr, __fmul_rn(vz, k.Rz));
+    const float vu = __fadd_rn(cp.pu, __fmul_rn(vz, k.Uz));
     const float den = __fmul_rn(vf, k.cF);
     const float a = __fdiv_rn(__fmul_rn(vr, k.cR), den);
     const float b = __fdiv_rn(__fmul_rn(vu, k.cU), den);
@@ -87,11 +107,14 @@ __device__ __forceinline__ bool project(const ScatterCam &k, const CamDev &c, fl
     const float pxf = floorf(__fmul_rn(__fadd_rn(a, wf), 0.5f));
     const float pyf = floorf(__fmul_rn(__fsub_rn(hf, b), 0.5f));
     if (!(pxf >= 0.0f && pxf < wf && pyf >= 0.0f && pyf < hf)) return false;
-    const float d = __fsqrt_rn(dot3(vx, vy, vz, vx, vy, vz));
+    const float d = __fsqrt_rn(__fadd_rn(cp.pd, __fmul_rn(vz, vz)));
     q = __float2uint_rz(fminf(__fmul_rn(d, qscale), kQMax));
     pix = (uint32_t)pyf * c.w + (uint32_t)pxf;
     return true;
 }
+
+// column fractions m / (nz - 1) held in shared memory up to this count
+constexpr int kScatterFracTable = 256;
 
 __global__ void k_scatter_clear(const RenderParams p) {
     const CamDev &c = p.cams[blockIdx.y];
@@ -102,6 +125,11 @@ __global__ void k_scatter_clear(const RenderParams p) {
 
 __global__ void __launch_bounds__(kScatterThreads) k_scatter(const RenderParams p,
                                                              const ScatterParams s) {
+    __shared__ float s_tm[kScatterFracTable];
+    const float zden = (float)(s.nz - 1);
+    for (uint32_t m = threadIdx.x; m < min(s.nz, (uint32_t)kScatterFracTable); m += blockDim.x)
+        s_tm[m] = __fdiv_rn((float)m, zden);
+    __syncthreads();
     const uint32_t cam = blockIdx.y;
     const CamDev &c = p.cams[cam];
     const float4 fp = reinterpret_cast<const float4 *>(p.cams + p.hdr->n_cams)[cam];
@@ -125,14 +153,14 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(const RenderParams 
     const bool slab = b2 > b0;  // node form: a slab exactly when its top is above the floor
     const float h0 = (float)b0, h1 = (float)b1, h2 = (float)b2;
     const float qscale = __fdiv_rn(kQMax, s.depth_max);
-    const float zden = (float)(s.nz - 1);
+    const ColumnPartials cp = column_partials(k, x, y);
     uint32_t *buf = c.hit_cell;
     for (uint32_t m = 0; m < s.nz; ++m) {
-        const float tm = __fdiv_rn((float)m, zden);
+        const float tm = m < (uint32_t)kScatterFracTable ? s_tm[m] : __fdiv_rn((float)m, zden);
         uint32_t pix, q;
-        if (project(k, c, qscale, x, y, __fsub_rn(h0, __fmul_rn(h0, tm)), pix, q))
+        if (project(k, c, qscale, cp, __fsub_rn(h0, __fmul_rn(h0, tm)), pix, q))
             atomicMin(buf + pix, (q << 8) | mat);
-        if (slab && project(k, c, qscale, x, y, __fadd_rn(h2, __fmul_rn(__fsub_rn(h1, h2), tm)),
+        if (slab && project(k, c, qscale, cp, __fadd_rn(h2, __fmul_rn(__fsub_rn(h1, h2), tm)),
                             pix, q))
             atomicMin(buf + pix, (q << 8) | mat | 8u);
     }

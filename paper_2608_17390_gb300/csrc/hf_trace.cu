@@ -235,7 +235,20 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const LevelDev *lvt
     uint8_t entry = kFaceInside;
 
 
-    for (int it = 0; it < max_steps; ++it) {
+    for (int it = 0;; ++it) {
+        // one bounds check per iteration, after every advance, ascent or
+        // descent: an index past the level's end, or below 0, means the ray
+        // has left the grid.  An ascent keeps the crossed axis out of range
+        // (it follows a step onto an even index n >= ceil(E / 2^l), so
+        // n / 2 >= ceil(E / 2^(l+1)); or onto -1, and -1 >> 1 = -1).  At an
+        // exact corner the other axis may come back in range, in a partial
+        // node past the grid's edge; the ray only moves further out, and a
+        // descent there lands on an out-of-range child, so it still misses.
+        // A ray that leaves on its last allowed iteration is a miss, not a
+        // step-limit error.
+        const LevelDev lv = lvt[level];
+        if ((uint32_t)nx >= lv.stride || (uint32_t)ny >= lv.rows) return;
+        if (it == max_steps) break;
         const int32_t bx = (nx + px) << level;  // exit boundary (cells)
         const int32_t by = (ny + py) << level;
         const int32_t numx = gx * (bx << kShift) + kx;  // > 0
@@ -248,7 +261,6 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const LevelDev *lvt
         // level; for a single cell the emptiness test below is exact (the
         // segment's z range [zlo, zhi] misses (-inf, h0] and [h1, h2] exactly
         // when zlo > top, or zlo > h0 and zhi < h1)
-        const LevelDev lv = lvt[level];
         const uint32_t word =
             PAIR && level == 0
                 ? pair_node(__ldg(lv.base + (uint32_t)ny * (lv.stride >> 1) + ((uint32_t)nx >> 1)),
@@ -283,7 +295,6 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const LevelDev *lvt
                 // a corner: the ray enters the cell through its Y side and an
                 // X cell boundary at the same instant; report the X face
                 if (lx == rx && adx != 0 && entry == face_y) entry = face_x;
-                if ((uint32_t)nx >= lvt[level].stride || (uint32_t)ny >= lvt[level].rows) return;
                 continue;
             }
             // a non-empty cell holds the hit: find its layer, face and time
@@ -301,7 +312,6 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const LevelDev *lvt
         entry = cmp <= 0 ? face_x : face_y;
         tin_num = tout_num;
         tin_den = tout_den;
-        if ((uint32_t)nx >= lv.stride || (uint32_t)ny >= lv.rows) return;
         // ascend when the crossed boundary is a parent boundary: the new index
         // on the crossed axis is then even (odd for a negative direction)
         const int32_t crossed = cmp <= 0 ? (nx ^ qx) : (ny ^ qy);
