@@ -297,13 +297,19 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const LevelDev *lvt
                 if (lx == rx && adx != 0 && entry == face_y) entry = face_x;
                 continue;
             }
-            // a non-empty cell holds the hit: find its layer, face and time
-            if (leaf_test(r, word, tin_num, tin_den, tout_num, tout_den, entry, h)) {
-                h.cx = nx;
-                h.cy = ny;
-                h.word = word;
+            // a non-empty cell holds the hit (the cell test is exact: the
+            // segment's z range meets (-inf, h0] or [h1, h2], and z is
+            // continuous along it): find its layer, face and time.  The
+            // advance below is reached from empty nodes and cells only.
+            if (!leaf_test(r, word, tin_num, tin_den, tout_num, tout_den, entry, h)) {
+                h.face = kFaceError;  // unreachable: reported, never silent
+                h.layer = 255;
                 return;
             }
+            h.cx = nx;
+            h.cy = ny;
+            h.word = word;
+            return;
         }
         // advance past the node (or cell) through its exit side; at an exact
         // corner both indices change and the X face is reported
