@@ -320,12 +320,12 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const LevelDev *lvt
         tin_den = tout_den;
         // ascend when the crossed boundary is a parent boundary: the new index
         // on the crossed axis is then even (odd for a negative direction)
+        // (as arithmetic, not a branch: one control path for every lane)
         const int32_t crossed = cmp <= 0 ? (nx ^ qx) : (ny ^ qy);
-        if (level < mip_start && (crossed & 1) == 0) {
-            ++level;
-            nx >>= 1;
-            ny >>= 1;
-        }
+        const int32_t up = (level < mip_start ? 1 : 0) & ~crossed & 1;
+        level += up;
+        nx >>= up;
+        ny >>= up;
     }
     h.face = kFaceError;
     h.layer = 255;
