@@ -150,17 +150,22 @@ def test_c2_full_size_sampled(hf):
 
 
 def test_c3_full_size_sampled(hf):
-    """The benchmark's launch configuration: 64 cameras, one batched launch,
-    shadow rays, default tile and mip start."""
+    """The benchmark's workload at full size: 64 cameras, one batched launch,
+    shadow rays; the library's default tile and mip start, and the tuned
+    launch the benchmark times (4 x 32 tiles, mip start 5)."""
     cfg = synth.config_c3()
     cells, cams = cfg["cells"], cfg["cams"]
     ctx = _ctx(hf, cells)
     try:
         pix = [sample_pixels(int(c["w"]), int(c["h"]), 300, 100 + i) for i, c in enumerate(cams)]
-        g = _gather(hf, ctx, cams, pix, True, hf.make_opts(flags=hf.HF_SHADOWS))
+        runs = {"default": _gather(hf, ctx, cams, pix, True, hf.make_opts(flags=hf.HF_SHADOWS)),
+                "4x32 mip 5": _gather(hf, ctx, cams, pix, True,
+                                      hf.make_opts(tile_w=4, tile_h=32, mip_start=5,
+                                                   flags=hf.HF_SHADOWS))}
         for i, c in enumerate(cams):
             o = oracle.render(cells, c, shadows=True, pix=pix[i], nthreads=NT)
-            compare(g[i], o, shadows=True, what="C3 cam %d" % i)
+            for name, g in runs.items():
+                compare(g[i], o, shadows=True, what="C3 %s cam %d" % (name, i))
     finally:
         hf.hf_destroy(ctx)
 
@@ -171,10 +176,13 @@ def test_c4_sampled_frames(hf):
     ctx = _ctx(hf, cells)
     try:
         pix = [sample_pixels(1920, 1080, 1500, 200 + i) for i in range(len(frames))]
-        g = _gather(hf, ctx, frames, pix, False, hf.make_opts())
+        runs = {"default": _gather(hf, ctx, frames, pix, False, hf.make_opts()),
+                "4x32 mip 9": _gather(hf, ctx, frames, pix, False,
+                                      hf.make_opts(tile_w=4, tile_h=32, mip_start=9))}
         for i, c in enumerate(frames):
             o = oracle.render(cells, c, pix=pix[i], nthreads=NT)
-            compare(g[i], o, what="C4 frame %d" % (100 * i))
+            for name, g in runs.items():
+                compare(g[i], o, what="C4 %s frame %d" % (name, 100 * i))
     finally:
         hf.hf_destroy(ctx)
 
