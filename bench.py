@@ -403,9 +403,12 @@ def run_hf(args):
 
     # end to end through the public API with host buffers: host camera records
     # and edit cells in, every output field back in pinned host memory, timed
-    # on the host clock around the whole call.  Path 1 (reported): the kernel
-    # writes the pinned host buffers itself (HF_HOST_OUTPUTS).  Path 2
-    # (context): device buffers, then one copy per output field.
+    # on the host clock around the whole call.  Two library paths, the faster
+    # reported: the kernel writes the pinned host buffers itself
+    # (HF_HOST_OUTPUTS), or renders chunks into device staging that the copy
+    # engine moves back while later chunks render (HF_HOST_STAGED).  For
+    # context: device buffers, then one copy per output field (each field of
+    # all cameras is one allocation, see alloc_outputs).
     e2e = e2e_copy = None
     if not args.no_e2e:
         host = hf.alloc_outputs(max_cams, device="pinned", shadows=wl["shadows"])
@@ -439,9 +442,9 @@ def run_hf(args):
                 else:
                     hf.hf_render(ctx, max_cams, outs[:len(max_cams)], opts)
                     with torch.cuda.stream(stream):
-                        for o, h in zip(outs, host):
-                            for k in o:
-                                h[k].copy_(o[k], non_blocking=True)
+                        for k in outs[0]:
+                            host[0][k].untyped_storage().copy_(outs[0][k].untyped_storage(),
+                                                               non_blocking=True)
                 stream.synchronize()
                 ems.append(time.perf_counter() - t0)
             return n_rays(max_cams) / float(np.median(ems))

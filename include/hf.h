@@ -71,12 +71,14 @@ extern "C" {
 #define HF_NOGRAPH 16u /* launch directly instead of replaying a captured CUDA graph */
 #define HF_NOWAIT 32u /* return HF_E_BUSY instead of waiting for a free render slot */
 #define HF_SCATTER_RAW 128u /* hf_render_scatter: leave the packed words in hit_cell, no resolve */
-#define HF_HOST_STAGED 256u /* the output buffers are pinned HOST memory: the library renders the
-                               cameras in about 16 contiguous chunks into its own device staging
-                               (four buffers of the largest chunk, allocated on first use) and
-                               copies each finished chunk back on a copy stream while later
-                               chunks render (hf_render only; not with HF_HOST_OUTPUTS, HF_PLAIN
-                               or HF_NOWAIT) */
+#define HF_HOST_STAGED 256u /* the output buffers are pinned HOST memory: the library renders
+                               chunks of consecutive cameras (about 1/16 of the pixels each,
+                               then halving chunks for the last eighth) into its own device
+                               staging (four buffers of the largest chunk, allocated on first
+                               use) and copies each finished chunk back on a copy stream while
+                               later chunks render; cameras whose host buffers of one field lie
+                               back to back share one copy (hf_render only; not with
+                               HF_HOST_OUTPUTS, HF_PLAIN or HF_NOWAIT) */
 #define HF_HOST_OUTPUTS 64u /* the output buffers are pinned HOST memory (cudaHostAlloc or
                                cudaHostRegister): the kernel writes the results there itself,
                                over the host link, with no separate copy (hf_render only) */

@@ -454,20 +454,25 @@ def hf_stats(ctx):
 
 def alloc_outputs(cams, device="cuda", shadows=False, fields=OUTPUT_FIELDS):
     """Allocate one dict of tensors per camera (torch): on `device`, or in
-    pinned host memory when device is "pinned" (for HF_HOST_OUTPUTS)."""
+    pinned host memory when device is "pinned" (for HF_HOST_OUTPUTS and
+    HF_HOST_STAGED).  Each field is one allocation for all cameras, and a
+    camera's tensor is a view of its slice, so consecutive cameras' buffers
+    are adjacent (the staged host path then copies a chunk's field at once)."""
     import torch
     dt = dict(hit_cell=torch.int32, layer=torch.uint8, face=torch.uint8, depth=torch.float32,
               rgba=torch.int32, shadow=torch.uint8)
-    outs = []
-    for c in camera_records(cams):
-        n = int(c["w"]) * int(c["h"])
-        o = {}
-        for k in fields:
-            if k == "shadow" and not shadows:
-                continue
-            if device == "pinned":
-                o[k] = torch.empty(n, dtype=dt[k], pin_memory=True)
-            else:
-                o[k] = torch.empty(n, dtype=dt[k], device=device)
-        outs.append(o)
+    sizes = [int(c["w"]) * int(c["h"]) for c in camera_records(cams)]
+    total = sum(sizes)
+    outs = [{} for _ in sizes]
+    for k in fields:
+        if k == "shadow" and not shadows:
+            continue
+        if device == "pinned":
+            block = torch.empty(total, dtype=dt[k], pin_memory=True)
+        else:
+            block = torch.empty(total, dtype=dt[k], device=device)
+        start = 0
+        for o, n in zip(outs, sizes):
+            o[k] = block[start:start + n]
+            start += n
     return outs

@@ -71,12 +71,14 @@ struct hf_ctx {
     uint32_t *d_vox = nullptr;  // voxel occupancy pyramid (hf_voxel_build), or null
     size_t vox_words = 0;
     hf::VoxelDev vd{};
-    // HF_HOST_STAGED: two device staging buffers the chunks render into, and the
-    // copy stream that streams each finished chunk to the caller's host buffers
+    // HF_HOST_STAGED: a ring of device staging buffers the chunks render into,
+    // the copy stream that streams each finished chunk to the caller's host
+    // buffers, and a second render stream (chunks alternate between the
+    // caller's stream and it, so one chunk's launch tail overlaps the next)
     char *d_hstage = nullptr;
     size_t hstage_half = 0;  // bytes of one staging buffer
-    cudaStream_t copy_stream = nullptr;
-    cudaEvent_t stage_ready[4] = {}, stage_free[4] = {};
+    cudaStream_t copy_stream = nullptr, render2 = nullptr;
+    cudaEvent_t stage_ready[4] = {}, stage_free[4] = {}, stage_start = nullptr;
     bool stage_busy[4] = {};
 };
 
@@ -311,10 +313,15 @@ int hf_destroy(hf_ctx *c) {
     if (c->d_stats) cudaFree(c->d_stats);
     if (c->d_world) cudaFree(c->d_world);
     if (c->d_vox) cudaFree(c->d_vox);
+    if (c->render2) {
+        if (cudaStreamSynchronize(c->render2) != cudaSuccess) rc = HF_E_CUDA;
+        cudaStreamDestroy(c->render2);
+    }
     if (c->copy_stream) {
         if (cudaStreamSynchronize(c->copy_stream) != cudaSuccess) rc = HF_E_CUDA;
         cudaStreamDestroy(c->copy_stream);
     }
+    if (c->stage_start) cudaEventDestroy(c->stage_start);
     for (int b = 0; b < 4; ++b) {
         if (c->stage_ready[b]) cudaEventDestroy(c->stage_ready[b]);
         if (c->stage_free[b]) cudaEventDestroy(c->stage_free[b]);
@@ -848,38 +855,47 @@ static int render_host_staged(hf_ctx *c, const hf_camera *cams, uint32_t n, cons
             if (a.type != cudaMemoryTypeHost) return HF_E_INVALID_ARG;  // pinned host memory only
         }
     }
-    // chunks: contiguous cameras, about total / kStageChunks pixels each
+    // chunks of consecutive cameras: about total / kStageChunks pixels each
+    // until an eighth of the pixels is left, then halving chunks (down to
+    // total / 128), so that the last copy, which nothing overlaps, is small
+    // (cameras ordered largest first make those chunks fine-grained)
     std::vector<uint32_t> first;
     {
-        const uint64_t target = (total_px + kStageChunks - 1) / kStageChunks;
-        uint64_t acc = 0;
+        uint64_t done = 0, acc = 0;
         first.push_back(0);
         for (uint32_t i = 0; i < n; ++i) {
             acc += (uint64_t)cams[i].w * cams[i].h;
+            const uint64_t left = total_px - done;  // pixels from this chunk's first camera on
+            const uint64_t target = left > total_px / 8
+                                        ? (total_px + kStageChunks - 1) / kStageChunks
+                                        : std::max<uint64_t>(left / 2, total_px / 128);
             if (acc >= target && i + 1 < n) {
                 first.push_back(i + 1);
+                done += acc;
                 acc = 0;
             }
         }
         first.push_back(n);
     }
-    auto cam_stage_bytes = [&](uint32_t i) {
+    // staging layout of a chunk: field by field, the chunk's cameras back to
+    // back (so that cameras whose host buffers are adjacent need one copy)
+    auto chunk_stage_bytes = [&](uint32_t i0, uint32_t i1) {
         size_t b = 0;
         for (int f = 0; f < 6; ++f) {
-            const size_t fb = field_bytes(outs[i], f) * cams[i].w * cams[i].h;
+            size_t fb = 0;
+            for (uint32_t i = i0; i < i1; ++i) fb += field_bytes(outs[i], f) * cams[i].w * cams[i].h;
             b += (fb + kAlign - 1) & ~(kAlign - 1);
         }
         return b;
     };
     size_t need = 0;
-    for (size_t k = 0; k + 1 < first.size(); ++k) {
-        size_t b = 0;
-        for (uint32_t i = first[k]; i < first[k + 1]; ++i) b += cam_stage_bytes(i);
-        need = std::max(need, b);
-    }
+    for (size_t k = 0; k + 1 < first.size(); ++k)
+        need = std::max(need, chunk_stage_bytes(first[k], first[k + 1]));
     CK(cudaSetDevice(c->device));
     cudaStream_t s = o.cuda_stream ? (cudaStream_t)o.cuda_stream : c->stream;
     if (!c->copy_stream) {
+        CK(cudaStreamCreateWithFlags(&c->render2, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c->stage_start, cudaEventDisableTiming));
         CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
         for (int b = 0; b < 4; ++b) {
             CK(cudaEventCreateWithFlags(&c->stage_ready[b], cudaEventDisableTiming));
@@ -887,6 +903,7 @@ static int render_host_staged(hf_ctx *c, const hf_camera *cams, uint32_t n, cons
         }
     }
     if (need > c->hstage_half) {  // grow: nothing may still use the old buffers
+        CK(cudaStreamSynchronize(c->render2));
         CK(cudaStreamSynchronize(c->copy_stream));
         for (int b = 0; b < 4; ++b) c->stage_busy[b] = false;
         sync_slots(c);
@@ -905,40 +922,68 @@ static int render_host_staged(hf_ctx *c, const hf_camera *cams, uint32_t n, cons
     inner.flags &= ~(HF_HOST_STAGED | HF_HOST_OUTPUTS | HF_SYNC);
     inner.cuda_stream = s;
     std::vector<hf_outputs> dev;
+    // the second render stream starts after the work already on the caller's
+    const cudaStream_t rs[2] = {s, c->render2};
+    CK(cudaEventRecord(c->stage_start, s));
+    CK(cudaStreamWaitEvent(c->render2, c->stage_start, 0));
     for (size_t k = 0; k + 1 < first.size(); ++k) {
         const int b = (int)(k % kBuffers);
-        if (c->stage_busy[b]) CK(cudaStreamWaitEvent(s, c->stage_free[b], 0));
+        const cudaStream_t ks = rs[k & 1];
+        if (c->stage_busy[b]) CK(cudaStreamWaitEvent(ks, c->stage_free[b], 0));
         char *base = c->d_hstage + b * c->hstage_half;
-        dev.assign(first[k + 1] - first[k], hf_outputs{});
+        const uint32_t i0 = first[k], i1 = first[k + 1];
+        dev.assign(i1 - i0, hf_outputs{});
         size_t off = 0;
-        for (uint32_t i = first[k]; i < first[k + 1]; ++i) {
-            hf_outputs &d = dev[i - first[k]];
-            void *slots[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-            for (int f = 0; f < 6; ++f) {
+        for (int f = 0; f < 6; ++f) {
+            for (uint32_t i = i0; i < i1; ++i) {
                 const size_t fb = field_bytes(outs[i], f) * cams[i].w * cams[i].h;
                 if (!fb) continue;
-                slots[f] = base + off;
-                off += (fb + kAlign - 1) & ~(kAlign - 1);
+                void *slot = base + off;
+                off += fb;
+                hf_outputs &d = dev[i - i0];
+                switch (f) {
+                    case 0: d.hit_cell = (uint32_t *)slot; break;
+                    case 1: d.layer = (uint8_t *)slot; break;
+                    case 2: d.face = (uint8_t *)slot; break;
+                    case 3: d.depth = (float *)slot; break;
+                    case 4: d.rgba = (uint32_t *)slot; break;
+                    default: d.shadow = (uint8_t *)slot; break;
+                }
             }
-            d.hit_cell = (uint32_t *)slots[0];
-            d.layer = (uint8_t *)slots[1];
-            d.face = (uint8_t *)slots[2];
-            d.depth = (float *)slots[3];
-            d.rgba = (uint32_t *)slots[4];
-            d.shadow = (uint8_t *)slots[5];
+            off = (off + kAlign - 1) & ~(kAlign - 1);
         }
-        const int rc = hf_render(c, cams + first[k], first[k + 1] - first[k], dev.data(), &inner);
+        inner.cuda_stream = ks;
+        const int rc = hf_render(c, cams + i0, i1 - i0, dev.data(), &inner);
         if (rc != HF_OK) return rc;
-        CK(cudaEventRecord(c->stage_ready[b], s));
+        CK(cudaEventRecord(c->stage_ready[b], ks));
         CK(cudaStreamWaitEvent(c->copy_stream, c->stage_ready[b], 0));
-        for (uint32_t i = first[k]; i < first[k + 1]; ++i) {
-            const hf_outputs &d = dev[i - first[k]];
-            const void *src[6] = {d.hit_cell, d.layer, d.face, d.depth, d.rgba, d.shadow};
-            for (int f = 0; f < 6; ++f) {
-                const size_t fb = field_bytes(outs[i], f) * cams[i].w * cams[i].h;
-                if (fb)
-                    CK(cudaMemcpyAsync(field_ptr(outs[i], f), src[f], fb, cudaMemcpyDeviceToHost,
+        // one copy per run of cameras whose host buffers of this field are
+        // adjacent (their staging is adjacent by construction)
+        for (int f = 0; f < 6; ++f) {
+            char *run_dst = nullptr;
+            const char *run_src = nullptr;
+            size_t run_bytes = 0;
+            for (uint32_t i = i0; i <= i1; ++i) {
+                size_t fb = 0;
+                char *dst = nullptr;
+                const char *src = nullptr;
+                if (i < i1) {
+                    fb = field_bytes(outs[i], f) * cams[i].w * cams[i].h;
+                    dst = static_cast<char *>(field_ptr(outs[i], f));
+                    const hf_outputs &d = dev[i - i0];
+                    const void *srcs[6] = {d.hit_cell, d.layer, d.face, d.depth, d.rgba, d.shadow};
+                    src = static_cast<const char *>(srcs[f]);
+                }
+                if (run_bytes && fb && dst == run_dst + run_bytes && src == run_src + run_bytes) {
+                    run_bytes += fb;
+                    continue;
+                }
+                if (run_bytes)
+                    CK(cudaMemcpyAsync(run_dst, run_src, run_bytes, cudaMemcpyDeviceToHost,
                                        c->copy_stream));
+                run_dst = dst;
+                run_src = src;
+                run_bytes = fb;
             }
         }
         CK(cudaEventRecord(c->stage_free[b], c->copy_stream));

@@ -564,7 +564,8 @@ def test_host_staged_outputs_equal_device_outputs(hf, c1):
     """HF_HOST_STAGED: the library renders chunks into its own staging and
     copies each back while the next renders; the host buffers equal a device
     render bit for bit, for one camera and for a multi-chunk batch with some
-    fields absent; pageable memory and conflicting flags are refused."""
+    fields absent, with each field's buffers back to back (one copy per run)
+    and apart; pageable memory and conflicting flags are refused."""
     import torch
 
     for cells, cams, fields, sh in (
@@ -575,8 +576,11 @@ def test_host_staged_outputs_equal_device_outputs(hf, c1):
         try:
             flags = hf.HF_SHADOWS if sh else 0
             dev = gpu_render(hf, ctx, cams, shadows=sh, opts=hf.make_opts(flags=flags), fields=fields)
-            for rep in range(2):  # the second call reuses the staging buffers
+            for rep in range(3):  # later calls reuse the staging buffers
                 host = hf.alloc_outputs(cams, device="pinned", shadows=sh, fields=fields)
+                if rep == 2:  # one allocation per camera and field: no two buffers adjacent
+                    host = [{k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
+                             for k, v in o.items()} for o in host]
                 hf.hf_render(ctx, cams, host, hf.make_opts(flags=flags | hf.HF_HOST_STAGED | hf.HF_SYNC))
                 for i in range(len(cams)):
                     for k, t in host[i].items():
