@@ -197,7 +197,10 @@ __device__ __forceinline__ bool vertical_test(const Ray &r, uint32_t word, Hit &
 // is the midline of exactly one sub-level, so a ray that enters a cell through
 // its Y side while also crossing an X cell boundary (a corner) is detected on
 // the way down and reported with the X face.
-template <bool STATS, bool PAIR>
+// EMPTY_FIRST picks the order of the two outcomes of the node test in the
+// code (empty: advance; else descend or hit); which order runs faster depends
+// on the kernel (measured: empty first with shadow rays, the other without).
+template <bool STATS, bool PAIR, bool EMPTY_FIRST>
 __device__ __forceinline__ void trace_ray(const WorldDev &w, const LevelDev *lvt, const Ray &r,
                                           int start_level, int mip_start, int max_steps, Hit &h,
                                           Counters &cnt) {
@@ -279,7 +282,28 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const LevelDev *lvt
         const bool empty = zd(r.oz - (maxtop << kShift), r.dz, lo_num, lo_den) > 0 ||
                            (zd(r.oz - (maxh0 << kShift), r.dz, lo_num, lo_den) > 0 &&
                             zd(r.oz - (minh1 << kShift), r.dz, hi_num, hi_den) < 0);
-        if (!empty) {
+        // advance past the node (or cell) through its exit side; at an exact
+        // corner both indices change and the X face is reported
+        auto advance = [&]() {
+            if (cmp <= 0) nx += gx;
+            if (cmp >= 0) ny += gy;
+            entry = cmp <= 0 ? face_x : face_y;
+            tin_num = tout_num;
+            tin_den = tout_den;
+            // ascend when the crossed boundary is a parent boundary: the new index
+            // on the crossed axis is then even (odd for a negative direction)
+            // (as arithmetic, not a branch: one control path for every lane)
+            const int32_t crossed = cmp <= 0 ? (nx ^ qx) : (ny ^ qy);
+            const int32_t up = (level < mip_start ? 1 : 0) & ~crossed & 1;
+            level += up;
+            nx >>= up;
+            ny >>= up;
+        };
+        if (EMPTY_FIRST && empty) {
+            advance();
+            continue;
+        }
+        if (EMPTY_FIRST || !empty) {
             if (level > 0) {
                 // descend into the child that holds the ray just after t_in:
                 // the upper child on an axis when the ray has passed that
@@ -300,7 +324,7 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const LevelDev *lvt
             // a non-empty cell holds the hit (the cell test is exact: the
             // segment's z range meets (-inf, h0] or [h1, h2], and z is
             // continuous along it): find its layer, face and time.  The
-            // advance below is reached from empty nodes and cells only.
+            // advance is reached from empty nodes and cells only.
             if (!leaf_test(r, word, tin_num, tin_den, tout_num, tout_den, entry, h)) {
                 h.face = kFaceError;  // unreachable: reported, never silent
                 h.layer = 255;
@@ -311,21 +335,7 @@ __device__ __forceinline__ void trace_ray(const WorldDev &w, const LevelDev *lvt
             h.word = word;
             return;
         }
-        // advance past the node (or cell) through its exit side; at an exact
-        // corner both indices change and the X face is reported
-        if (cmp <= 0) nx += gx;
-        if (cmp >= 0) ny += gy;
-        entry = cmp <= 0 ? face_x : face_y;
-        tin_num = tout_num;
-        tin_den = tout_den;
-        // ascend when the crossed boundary is a parent boundary: the new index
-        // on the crossed axis is then even (odd for a negative direction)
-        // (as arithmetic, not a branch: one control path for every lane)
-        const int32_t crossed = cmp <= 0 ? (nx ^ qx) : (ny ^ qy);
-        const int32_t up = (level < mip_start ? 1 : 0) & ~crossed & 1;
-        level += up;
-        nx >>= up;
-        ny >>= up;
+        advance();
     }
     h.face = kFaceError;
     h.layer = 255;
@@ -395,7 +405,7 @@ __device__ __forceinline__ void trace_pixel(const RenderParams &p, const LevelDe
         // same traversal code together
         const bool sp = SHADOWS && shadow_pass;
         Counters pc{0, 0};
-        trace_ray<STATS, PAIR>(p.world, lvt, r, sp ? min(kShadowStart, p.shadow_mip) : start,
+        trace_ray<STATS, PAIR, SHADOWS>(p.world, lvt, r, sp ? min(kShadowStart, p.shadow_mip) : start,
                                sp ? p.shadow_mip : p.mip_start, p.max_steps, h, pc);
         if (STATS) {
             Counters &dst = sp ? scnt : cnt;
