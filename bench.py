@@ -258,9 +258,11 @@ def run_hf(args):
 
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
+        if local == 0:  # one build per node; the other ranks wait for it
+            __graft_entry__.build_library()
+        dist.barrier()
     else:
         torch.cuda.set_device(0)
-    if rank == 0 or ws > 1:
         __graft_entry__.build_library()
     import paper_2608_17390_gb300 as hf
     import synth
@@ -507,7 +509,7 @@ def run_hf(args):
         "clocks": ck,
         "e2e": e2e,
     }
-    if not args.no_cpu:
+    if not args.no_cpu and ws == 1:  # the host-core oracle sample: rank 0 at N = 1 only
         line["cpu_baseline"] = cpu_oracle_sample(wl, budget_s=args.cpu_seconds)
     print(json.dumps(line))
     if ws > 1:

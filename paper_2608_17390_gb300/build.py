@@ -46,15 +46,21 @@ def build(verbose=False, extra=()):
         obj = os.path.join(OUT, src + ".o")
         objs.append(obj)
         if _stale(obj, [path] + headers) or extra:
-            cmd = [nvcc()] + _flags() + list(extra) + ["-c", path, "-o", obj]
-            jobs.append(cmd)
+            # written under a temporary name and renamed, so that concurrent
+            # builds (one per process) never leave a partial object
+            tmp = obj + ".tmp%d" % os.getpid()
+            cmd = [nvcc()] + _flags() + list(extra) + ["-c", path, "-o", tmp]
+            jobs.append((cmd, tmp, obj))
 
-    def run(cmd):
+    def run(job):
+        cmd, tmp, final = job if isinstance(job, tuple) else (job, None, None)
         r = subprocess.run(cmd, capture_output=True, text=True)
         if verbose or r.returncode:
             sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
         if r.returncode:
             raise RuntimeError("nvcc failed: " + " ".join(cmd))
+        if tmp:
+            os.replace(tmp, final)
 
     with ThreadPoolExecutor(max_workers=len(jobs) or 1) as ex:
         list(ex.map(run, jobs))
