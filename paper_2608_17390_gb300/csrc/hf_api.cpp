@@ -1041,9 +1041,11 @@ int hf_render(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_outputs *ou
     // one camera: the plain launch (its grid covers the camera's tiles) spares
     // the persistent kernel's shared tile counter, which small tiles contend on
     if ((o.flags & HF_PLAIN) || (n == 1 && !(o.flags & HF_NOGRAPH))) {
-        CK(cudaMemcpyAsync(s.d_scratch, s.h_staging, b.bytes, cudaMemcpyHostToDevice, b.stream));
+        // each launch takes its camera record as a parameter: no copy to the device
+        const auto *cd = (const hf::CamDev *)((const char *)s.h_staging + sizeof(hf::BatchHeader));
         for (uint32_t i = 0; i < n; ++i)
-            if (hf::launch_trace_plain(p, shadows, stats, i, b.tiles[i], b.stream)) return HF_E_CUDA;
+            if (hf::launch_trace_plain(p, shadows, stats, cd[i], b.tiles[i], b.stream))
+                return HF_E_CUDA;
     } else if (o.flags & HF_NOGRAPH) {
         CK(cudaMemcpyAsync(s.d_scratch, s.h_staging, b.bytes, cudaMemcpyHostToDevice, b.stream));
         if (hf::launch_trace_batched(p, shadows, stats, c->sm_count * c->occ[shadows][stats],

@@ -183,7 +183,8 @@ int launch_voxel_trace(const RenderParams &p, const VoxelDev &v, const VoxelPara
 // The trace kernels are instantiated per level-0 storage; p.world.pair picks one.
 int launch_trace_batched(const RenderParams &p, bool shadows, bool stats, int blocks,
                          void *stream);
-int launch_trace_plain(const RenderParams &p, bool shadows, bool stats, uint32_t cam_index,
+// (the plain kernel takes its camera record as a launch parameter)
+int launch_trace_plain(const RenderParams &p, bool shadows, bool stats, const CamDev &cam,
                        uint32_t n_tiles, void *stream);
 const void *trace_batched_fn(bool shadows, bool stats, bool pair);
 int trace_batched_occupancy(bool shadows, bool stats, bool pair, int *blocks_per_sm);

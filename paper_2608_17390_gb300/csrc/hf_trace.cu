@@ -567,18 +567,19 @@ __global__ void __launch_bounds__(kThreads, HF_TRACE_MIN_BLOCKS) k_trace_batched
 }
 
 // Plain kernel: one camera, one warp per tile, grid covers the image once.
+// The camera record is a kernel parameter (read in place, uniform across the
+// grid), so a plain render needs no copy of it to the device.
 template <bool SHADOWS, bool STATS, bool PAIR>
-__global__ void __launch_bounds__(kThreads, HF_TRACE_MIN_BLOCKS) k_trace_plain(const RenderParams p, uint32_t cam,
-                                                          uint32_t n_tiles) {
-    __shared__ CamDev s_cam[kThreads / 32];
+__global__ void __launch_bounds__(kThreads, HF_TRACE_MIN_BLOCKS)
+    k_trace_plain(const __grid_constant__ RenderParams p, const __grid_constant__ CamDev cam,
+                  uint32_t n_tiles) {
     __shared__ LevelDev s_lv[kMaxLevels + 1];
     fill_levels(s_lv, p.world);
     __syncthreads();
     const uint32_t t = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
     if (t >= n_tiles) return;
     const int lane = threadIdx.x & 31;
-    const CamDev &c = stage_cam(&s_cam[threadIdx.x >> 5], p.cams, cam, lane);
-    trace_tile<SHADOWS, STATS, PAIR>(p, s_lv, c, t, lane);
+    trace_tile<SHADOWS, STATS, PAIR>(p, s_lv, cam, t, lane);
 }
 
 template <bool SH, bool ST, bool PA>
@@ -593,7 +594,7 @@ const void *batched_fn(bool shadows, bool stats) {
 }
 
 template <bool SH, bool ST, bool PA>
-void plain_launch(const RenderParams &p, uint32_t blocks, cudaStream_t s, uint32_t cam,
+void plain_launch(const RenderParams &p, uint32_t blocks, cudaStream_t s, const CamDev &cam,
                   uint32_t n_tiles) {
     k_trace_plain<SH, ST, PA><<<blocks, kThreads, 0, s>>>(p, cam, n_tiles);
 }
@@ -619,13 +620,13 @@ int launch_trace_batched(const RenderParams &p, bool shadows, bool stats, int bl
     return e == cudaSuccess ? 0 : -1;
 }
 
-int launch_trace_plain(const RenderParams &p, bool shadows, bool stats, uint32_t cam,
+int launch_trace_plain(const RenderParams &p, bool shadows, bool stats, const CamDev &cam,
                        uint32_t n_tiles, void *stream) {
     if (n_tiles == 0) return 0;
     cudaStream_t s = (cudaStream_t)stream;
     const uint32_t warps = kThreads / 32;
     const uint32_t blocks = (n_tiles + warps - 1) / warps;
-    using Fn = void (*)(const RenderParams &, uint32_t, cudaStream_t, uint32_t, uint32_t);
+    using Fn = void (*)(const RenderParams &, uint32_t, cudaStream_t, const CamDev &, uint32_t);
     static const Fn table[8] = {
         plain_launch<false, false, false>, plain_launch<false, false, true>,
         plain_launch<false, true, false>,  plain_launch<false, true, true>,
