@@ -518,6 +518,12 @@ def run_hf(args):
         dist.destroy_process_group()
 
 
+# serving lanes (streams) and requests per batch: swept at 70 % and 100 % load
+# (lanes 2/4/8/16, batches up to 8/32); 8 lanes of up to 8 requests gave the
+# lowest p99 frame latency at both loads
+SERVE_LANES, SERVE_MAX_BATCH = 8, 8
+
+
 def run_serve(args):
     """Serving loop on the large world: p50/p99 frame and edit-to-visible
     latency at ~70 % and ~100 % of the measured batched capacity."""
@@ -533,7 +539,7 @@ def run_serve(args):
     import synth
 
     cells = synth.config_c4()["cells"]
-    srv = serve.Server(cells, lanes=4, mem_bytes=4 << 30, max_batch=32)
+    srv = serve.Server(cells, lanes=SERVE_LANES, mem_bytes=4 << 30, max_batch=SERVE_MAX_BATCH)
     # capacity: one batched render of 64 representative requests
     probe = [r for r in synth.poisson_requests(cells, 72, 1.0, seed=99) if r["kind"] == "render"]
     cams = np.array([r["cam"] for r in probe])
@@ -574,8 +580,8 @@ def run_serve(args):
             "data": "synthetic",
             "config": {"workload": "C5 serving: 2048x16384 grid resident, Poisson render "
                                    "requests (640x360..3840x2160, random poses) with a 64x64 "
-                                   "crater edit every 11th request", "lanes": 4,
-                       "output_memory_budget_bytes": 4 << 30, "max_batch": 32},
+                                   "crater edit every 11th request", "lanes": SERVE_LANES,
+                       "output_memory_budget_bytes": 4 << 30, "max_batch": SERVE_MAX_BATCH},
             "capacity_rays_per_s": cap_rays, "capacity_requests_per_s": cap_req,
             "loads": results}
     print(json.dumps(line))
