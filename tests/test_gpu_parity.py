@@ -233,7 +233,8 @@ def test_edge_cases(hf):
     S = 65536
     rng = np.random.default_rng(7)
     cases = []
-    # 1 x 1 grid, non-power-of-two grid, a 16384-wide strip, height-zero floor
+    # 1 x 1 grid, non-power-of-two grid, 16384-wide and 16384-tall strips, an
+    # image of the largest width, height-zero floor
     cases.append((np.array([[synth.pack_cells(3, 5, 9, 2)]], np.uint32),
                   [synth.pose_to_camera(0.5, 0.5, 7.0, 0, -90, 60, 3, 3),
                    synth.pose_to_camera(0.0, 0.0, 4.0, 45, -10, 90, 5, 4)]))
@@ -244,6 +245,11 @@ def test_edge_cases(hf):
     wide = _rand_grid(rng, 16384, 16, 40)
     cases.append((wide, [synth.pose_to_camera(16383.9, 8.0, 30.0, 270, -1, 20, 97, 5),
                          synth.pose_to_camera(0.1, 8.0, 30.0, 90, -1, 20, 97, 5)]))
+    tall = _rand_grid(rng, 16, 16384, 40)
+    cases.append((tall, [synth.pose_to_camera(8.0, 16383.9, 30.0, 180, -1, 20, 97, 5),
+                         synth.pose_to_camera(8.0, 0.1, 30.0, 0, -1, 20, 97, 5)]))
+    cases.append((_rand_grid(rng, 37, 29, 30),
+                  [synth.pose_to_camera(18.5, 14.5, 40.0, 30, -30, 120, int(hf.HF_MAX_DIM), 2)]))
     cases.append((np.zeros((8, 8), np.uint32),
                   [synth.pose_to_camera(4.0, 4.0, 3.0, 0, -90, 90, 7, 7)]))
     for cells, poses in cases:
