@@ -62,12 +62,19 @@ TRACE_SOURCES = ("paper_2608_17390_gb300/csrc/hf_trace.cu", "paper_2608_17390_gb
 
 
 def trace_source_hash():
+    """Hash of the trace kernel's code: its sources with comments and blank
+    lines removed, so that the committed ncu figures stay attached to the
+    code they were measured on across edits of comments only."""
     import hashlib
+    import re
 
     h = hashlib.sha256()
     for rel in TRACE_SOURCES:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, rel)) as f:
+            src = f.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update("\n".join(l.rstrip() for l in src.splitlines() if l.strip()).encode())
     return h.hexdigest()[:16]
 
 

@@ -14,8 +14,12 @@
 //     known-empty space, Section 3.2 of the paper); otherwise the traversal
 //     descends; at level 0 the cell's two solid intervals are tested (the
 //     SOLID predicate of Section 3.1, closed ends, floor unbounded below);
-//   * after a node skip the coordinate along the other axis is an exact floor
-//     division with a float estimate and one integer correction.
+//   * a skip changes only the node index on the exit axis; the finer bits of
+//     the other axis are recovered on descent by exact midline tests (no
+//     division);
+//   * a shadow ray starts at the floor of the hit point (an exact floor
+//     division: a float estimate and one integer correction), one fixed-point
+//     unit outward along the face normal.
 #include <cuda_runtime.h>
 #include <math.h>
 
