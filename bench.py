@@ -563,24 +563,34 @@ def run_serve(args):
     mean_rays = n_rays(cams) / len(cams)
     cap_req = cap_rays / mean_rays * 10.0 / 11.0  # requests/s incl. 1 edit per 10 renders
     del outs
-    results = {}
+    # each load: the library's native loop (hf_serve_replay, reported), then the
+    # Python loop over the same request stream (for comparison)
+    results, py_results = {}, {}
     for load in (0.7, 1.0):
-        reqs = serve.requests_from(synth.poisson_requests(cells, args.serve_requests,
-                                                          load * cap_req, seed=int(load * 100)))
+        records = synth.poisson_requests(cells, args.serve_requests, load * cap_req,
+                                         seed=int(load * 100))
         t0 = time.perf_counter()
-        done = srv.run(reqs)
-        wall = time.perf_counter() - t0
-        st = serve.summarize(done, wall)
+        done = serve.run_native(srv.ctx, records, lanes=SERVE_LANES, max_batch=SERVE_MAX_BATCH,
+                                mem_bytes=4 << 30)
+        st = serve.summarize(done, time.perf_counter() - t0)
         st["offered_requests_per_s"] = load * cap_req
-        st["batches"] = srv.batches
-        st["max_inflight_batches"] = srv.max_inflight
+        st["batches"] = len({r.batch_id for r in done if r.kind == "render"})
         results["load_%d%%" % int(load * 100)] = st
+        b0 = srv.batches
+        t0 = time.perf_counter()
+        done = srv.run(serve.requests_from(records))
+        st = serve.summarize(done, time.perf_counter() - t0)
+        st["batches"] = srv.batches - b0
+        st["max_inflight_batches"] = srv.max_inflight
+        py_results["load_%d%%" % int(load * 100)] = st
     srv.close()
     if rank != 0:
         return
     hi = results["load_100%"]
     line = {"metric": "p50/p99 frame and edit-to-visible latency, serving loop (continuous "
                       "batching, 10 renders : 1 edit)",
+            "serving_loop": "native (hf_serve_replay); loads_python_loop: the same streams "
+                            "through the Python loop (serve.Server)",
             "value": hi["frame_ms_p99"], "unit": "ms (p99 frame latency at ~100% load)",
             "n_gpus": ws, "steps": args.serve_requests, "warmup": 0,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
@@ -590,7 +600,7 @@ def run_serve(args):
                                    "crater edit every 11th request", "lanes": SERVE_LANES,
                        "output_memory_budget_bytes": 4 << 30, "max_batch": SERVE_MAX_BATCH},
             "capacity_rays_per_s": cap_rays, "capacity_requests_per_s": cap_req,
-            "loads": results}
+            "loads": results, "loads_python_loop": py_results}
     print(json.dumps(line))
 
 

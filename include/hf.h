@@ -435,6 +435,59 @@ int hf_rebuild(hf_ctx *ctx);
  * Errors: HF_E_INVALID_ARG, HF_E_CUDA. */
 int hf_stats(hf_ctx *ctx, uint64_t out[5]);
 
+/* ---------------------------------------------------------------- serving
+ * A native serving loop over one resident world (the paper's interactive
+ * setting: renders and edits interleaved, an edit visible to the next frame,
+ * Section 4.4).  hf_serve_replay runs a stream of requests, each with its
+ * arrival time, on the calling thread: a request becomes visible to the loop
+ * when the host clock passes its arrival; renders are admitted in arrival
+ * order into batches (up to max_batch requests, within output_budget bytes
+ * of device output memory in flight) launched with hf_render on the first
+ * free lane (one CUDA stream per lane, so batches overlap on the device);
+ * an edit is applied with hf_edit when it reaches the head of the queue, so
+ * renders admitted before it do not see it and every later one does; a batch
+ * retires when its completion event has fired, and its output memory (from a
+ * pool the loop owns; the images are not kept) is released.
+ * Times are seconds from the start of the replay: `admitted` on the host
+ * clock, `done` the device completion of the request's batch (a reference
+ * event maps device time to the host clock) or, for an edit, the hf_edit
+ * call.  The loop returns when every request is done. */
+#define HF_REQ_RENDER 0u
+#define HF_REQ_EDIT 1u
+
+typedef struct {
+    uint32_t kind;        /* HF_REQ_RENDER or HF_REQ_EDIT */
+    uint32_t reserved;    /* 0 */
+    double arrival;       /* seconds after the start of the replay, non-decreasing */
+    hf_camera cam;        /* HF_REQ_RENDER: the view */
+    uint32_t x0, y0, w, h;/* HF_REQ_EDIT: the rectangle */
+    const uint32_t *cells;/* HF_REQ_EDIT: w*h host cells, rows back to back (copied by hf_edit) */
+} hf_request;
+
+typedef struct {
+    double admitted;      /* host time of admission (renders) or of the hf_edit call (edits) */
+    double done;          /* device completion of the batch (renders); the hf_edit call (edits) */
+    uint32_t version;     /* edits applied before admission (renders); this edit's number (edits) */
+    uint32_t batch;       /* batch index (renders); 0xFFFFFFFF for edits */
+} hf_request_result;
+
+typedef struct {
+    uint32_t lanes;          /* CUDA streams with a batch in flight each, 1..64 */
+    uint32_t max_batch;      /* renders per batch, 1..HF_MAX_CAMERAS */
+    uint64_t output_budget;  /* bytes of device output memory in flight at once */
+    uint32_t flags;          /* HF_SHADOWS (then a shadow byte per pixel is written too) */
+    uint32_t tile_w, tile_h, mip_start;  /* as hf_render_opts (0 tile sides, HF_MIP_AUTO: defaults) */
+} hf_serve_opts;
+
+/* Runs reqs[0..n) and fills results[0..n).  HF_E_INVALID_ARG for a bad
+ * option, a request of an unknown kind, arrivals out of order, or a render
+ * whose outputs exceed the whole budget (nothing is run then); errors of
+ * hf_render / hf_edit are returned as they occur (requests already launched
+ * are completed first).  The lanes and the pool are created and destroyed
+ * by the call. */
+int hf_serve_replay(hf_ctx *ctx, const hf_request *reqs, uint32_t n, const hf_serve_opts *opts,
+                    hf_request_result *results);
+
 #ifdef __cplusplus
 }
 #endif

@@ -126,6 +126,28 @@ class hf_info_t(ctypes.Structure):
                 ("reserved", ctypes.c_uint32)]
 
 
+class hf_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("arrival", ctypes.c_double), ("cam", hf_camera),
+                ("x0", ctypes.c_uint32), ("y0", ctypes.c_uint32), ("w", ctypes.c_uint32),
+                ("h", ctypes.c_uint32), ("cells", ctypes.c_void_p)]
+
+
+class hf_request_result(ctypes.Structure):
+    _fields_ = [("admitted", ctypes.c_double), ("done", ctypes.c_double),
+                ("version", ctypes.c_uint32), ("batch", ctypes.c_uint32)]
+
+
+class hf_serve_opts(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_uint32), ("max_batch", ctypes.c_uint32),
+                ("output_budget", ctypes.c_uint64), ("flags", ctypes.c_uint32),
+                ("tile_w", ctypes.c_uint32), ("tile_h", ctypes.c_uint32),
+                ("mip_start", ctypes.c_uint32)]
+
+
+HF_REQ_RENDER = 0
+HF_REQ_EDIT = 1
+
 # numpy view of hf_camera (same layout as the C struct)
 CAMERA_DTYPE = np.dtype(
     [("o", "<i8", (3,)), ("f", "<i4", (3,)), ("r", "<i4", (3,)),
@@ -162,6 +184,7 @@ _SIGS = {
     "hf_read_pyramid": ([_P, _U32, _P], ctypes.c_int),
     "hf_rebuild": ([_P], ctypes.c_int),
     "hf_stats": ([_P, _P], ctypes.c_int),
+    "hf_serve_replay": ([_P, _P, _U32, ctypes.POINTER(hf_serve_opts), _P], ctypes.c_int),
 }
 
 
@@ -450,6 +473,40 @@ def hf_stats(ctx):
     _check(lib.hf_stats(ctx, v), "hf_stats")
     return dict(node_fetches=v[0], cell_fetches=v[1], rays=v[2], shadow_rays=v[3],
                 shadow_fetches=v[4])
+
+
+def hf_serve_replay(ctx, records, lanes=8, max_batch=8, output_budget=4 << 30, flags=0,
+                    tile_w=0, tile_h=0, mip_start=HF_MIP_AUTO):
+    """Run a request stream through the library's native serving loop.
+    `records` are dicts with "kind" ("render" or "edit"), "arrival" (seconds
+    from the start, non-decreasing), "cam" (a camera record, renders) and
+    "edit" ((x0, y0, cells), edits).  Returns a numpy structured array of
+    (admitted, done, version, batch), one row per record."""
+    n = len(records)
+    reqs = (hf_request * n)()
+    keep = []  # the edit cells stay alive through the call
+    for i, rec in enumerate(records):
+        q = reqs[i]
+        q.arrival = float(rec["arrival"])
+        if rec["kind"] == "edit":
+            x0, y0, blk = rec["edit"]
+            blk = np.ascontiguousarray(blk, dtype=np.uint32)
+            keep.append(blk)
+            q.kind = HF_REQ_EDIT
+            q.x0, q.y0, q.h, q.w = int(x0), int(y0), blk.shape[0], blk.shape[1]
+            q.cells = blk.ctypes.data
+        else:
+            q.kind = HF_REQ_RENDER
+            c = camera_records(np.array([rec["cam"]]))
+            ctypes.memmove(ctypes.addressof(q.cam), c.ctypes.data, ctypes.sizeof(hf_camera))
+    res = (hf_request_result * n)()
+    opts = hf_serve_opts(lanes, max_batch, output_budget, flags, tile_w, tile_h, mip_start)
+    _check(lib.hf_serve_replay(ctx, ctypes.cast(reqs, _P) if n else None, n, ctypes.byref(opts),
+                               ctypes.cast(res, _P) if n else None), "hf_serve_replay")
+    out = np.zeros(n, dtype=[("admitted", "f8"), ("done", "f8"), ("version", "u4"), ("batch", "u4")])
+    for i in range(n):
+        out[i] = (res[i].admitted, res[i].done, res[i].version, res[i].batch)
+    return out
 
 
 def alloc_outputs(cams, device="cuda", shadows=False, fields=OUTPUT_FIELDS):

@@ -178,6 +178,27 @@ class Server:
         return completed
 
 
+def run_native(ctx, records, lanes=8, max_batch=8, mem_bytes=4 << 30, shadows=False, opts=None):
+    """The same request stream through the library's native serving loop
+    (hf_serve_replay: the loop above, written in C++ behind the C ABI, with no
+    Python between arrivals and launches).  Returns Request objects with the
+    admitted / done / version fields filled in, for summarize()."""
+    from . import hf_serve_replay
+
+    base = opts if opts is not None else make_opts()
+    res = hf_serve_replay(ctx, records, lanes=lanes, max_batch=max_batch, output_budget=mem_bytes,
+                          flags=HF_SHADOWS if shadows else 0, tile_w=base.tile_w,
+                          tile_h=base.tile_h, mip_start=base.mip_start)
+    out = requests_from(records)
+    for r, x in zip(out, res):
+        r.admitted, r.done, r.version = float(x["admitted"]), float(x["done"]), int(x["version"])
+        if r.kind == "edit":
+            r.call_time = r.admitted
+        else:
+            r.batch_id = int(x["batch"])
+    return out
+
+
 def requests_from(records):
     """Request objects from the plain records of synth.poisson_requests."""
     out = []

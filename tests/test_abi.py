@@ -139,6 +139,43 @@ def test_camera_dtype_matches_c_layout(hf):
     assert ctypes.sizeof(hf.hf_render_opts) == 40
 
 
+def test_struct_layouts_match_the_header(hf, tmp_path):
+    """sizeof / offsetof of the ABI's structs as the C compiler lays them out,
+    against the binding's ctypes mirrors."""
+    import shutil
+    import subprocess
+
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    fields = {"hf_camera": ("origin", "w"), "hf_outputs": ("hit_cell", "shadow"),
+              "hf_render_opts": ("tile_w", "cuda_stream"),
+              "hf_request": ("arrival", "cam", "x0", "cells"),
+              "hf_request_result": ("done", "batch"),
+              "hf_serve_opts": ("output_budget", "mip_start")}
+    lines = []
+    for t, fs in fields.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (t, t))
+        for f in fs:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (t, f, t, f))
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"hf.h\"\nint main(void) {\n"
+                   + "\n".join(lines) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                  check=True).stdout.splitlines())
+    for t, fs in fields.items():
+        ct = getattr(hf, t)
+        assert int(got[t]) == ctypes.sizeof(ct), t
+        for f in fs:
+            assert int(got["%s.%s" % (t, f)]) == getattr(ct, f).offset, (t, f)
+
+
+def test_serve_replay_rejects_before_touching_the_gpu(hf):
+    opts = hf.hf_serve_opts(8, 8, 1 << 30, 0, 0, 0, hf.HF_MIP_AUTO)
+    assert hf.lib.hf_serve_replay(None, None, 0, ctypes.byref(opts), None) == hf.HF_E_INVALID_ARG
+
+
 def test_pair_validation_agrees_with_the_oracle(hf):
     """The library's paired-texel check and the oracle's decoder-side check
     accept and reject the same grids, at the same first bad pair."""

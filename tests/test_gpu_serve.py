@@ -81,3 +81,57 @@ def test_each_result_same_alone_and_in_the_mix(hf):
         finally:
             hf.hf_destroy(ctx)
     assert checked == len(renders)
+
+
+def test_native_loop_orders_edits_and_leaves_the_edited_world(hf):
+    """hf_serve_replay: every render's version is the number of edits before it
+    in the stream, edits are numbered in order, times are sane, and the world
+    afterwards holds exactly the edited cells."""
+    from paper_2608_17390_gb300 import serve
+
+    cells, _ = synth.make_grid(512, 512, seed=13, slab_frac=0.3, n_walls=20)
+    records = synth.poisson_requests(cells, 120, rate=2e4, seed=5, edit_every=6,
+                                     resolutions=((160, 90), (320, 180), (96, 64), (640, 360)))
+    ctx = hf.hf_create(cells)
+    try:
+        done = serve.run_native(ctx, records, lanes=4, max_batch=3, mem_bytes=64 << 20)
+        edits_before = 0
+        world = cells.copy()
+        for rec, r in zip(records, done):
+            if rec["kind"] == "edit":
+                edits_before += 1
+                assert r.version == edits_before
+                x0, y0, blk = rec["edit"]
+                world[y0:y0 + blk.shape[0], x0:x0 + blk.shape[1]] = blk
+            else:
+                assert r.version == edits_before
+                assert r.admitted >= r.arrival - 1e-4 and r.done >= r.admitted - 1e-3
+        assert edits_before == sum(rec["kind"] == "edit" for rec in records) > 5
+        assert len({r.batch_id for r in done if r.kind == "render"}) > 3
+        stats = serve.summarize(done, 1.0)
+        assert stats["renders"] + stats["edits"] == 120 and stats["frame_ms_p99"] is not None
+        got = hf.hf_read_cells(ctx, 0, 0, 512, 512)
+        assert np.array_equal(got, world)
+    finally:
+        hf.hf_destroy(ctx)
+
+
+def test_native_loop_arguments_are_checked(hf):
+    cells, _ = synth.make_grid(64, 64, seed=2, slab_frac=0.3)
+    records = synth.poisson_requests(cells, 12, rate=1e4, seed=1, edit_every=5,
+                                     resolutions=((64, 48),))
+    ctx = hf.hf_create(cells)
+    try:
+        for kw in (dict(lanes=0), dict(lanes=65), dict(max_batch=0), dict(output_budget=0),
+                   dict(flags=hf.HF_PLAIN), dict(output_budget=1000)):
+            with pytest.raises(hf.HFError):
+                hf.hf_serve_replay(ctx, records, **kw)
+        late = [dict(r) for r in records]
+        late[3]["arrival"], late[4]["arrival"] = late[4]["arrival"] + 1.0, late[3]["arrival"]
+        with pytest.raises(hf.HFError):
+            hf.hf_serve_replay(ctx, late)
+        assert hf.hf_serve_replay(ctx, []).size == 0
+        res = hf.hf_serve_replay(ctx, records, lanes=2, max_batch=2, output_budget=1 << 20)
+        assert (res["done"] > 0).all()
+    finally:
+        hf.hf_destroy(ctx)
