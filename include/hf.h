@@ -447,7 +447,7 @@ int hf_stats(hf_ctx *ctx, uint64_t out[5]);
  * an edit is applied with hf_edit when it reaches the head of the queue, so
  * renders admitted before it do not see it and every later one does; a batch
  * retires when its completion event has fired, and its output memory (from a
- * pool the loop owns; the images are not kept) is released.
+ * pool the loop owns, unless the request names its own buffers) is released.
  * Times are seconds from the start of the replay: `admitted` on the host
  * clock, `done` the device completion of the request's batch (a reference
  * event maps device time to the host clock) or, for an edit, the hf_edit
@@ -462,6 +462,9 @@ typedef struct {
     hf_camera cam;        /* HF_REQ_RENDER: the view */
     uint32_t x0, y0, w, h;/* HF_REQ_EDIT: the rectangle */
     const uint32_t *cells;/* HF_REQ_EDIT: w*h host cells, rows back to back (copied by hf_edit) */
+    hf_outputs outs;      /* HF_REQ_RENDER, optional: caller-owned device buffers for the image
+                             (a NULL member is not written); all NULL: the loop renders into its
+                             own pool (counted against output_budget) and drops the image */
 } hf_request;
 
 typedef struct {

@@ -130,7 +130,7 @@ class hf_request(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
                 ("arrival", ctypes.c_double), ("cam", hf_camera),
                 ("x0", ctypes.c_uint32), ("y0", ctypes.c_uint32), ("w", ctypes.c_uint32),
-                ("h", ctypes.c_uint32), ("cells", ctypes.c_void_p)]
+                ("h", ctypes.c_uint32), ("cells", ctypes.c_void_p), ("outs", hf_outputs)]
 
 
 class hf_request_result(ctypes.Structure):
@@ -476,12 +476,14 @@ def hf_stats(ctx):
 
 
 def hf_serve_replay(ctx, records, lanes=8, max_batch=8, output_budget=4 << 30, flags=0,
-                    tile_w=0, tile_h=0, mip_start=HF_MIP_AUTO):
+                    tile_w=0, tile_h=0, mip_start=HF_MIP_AUTO, outputs=None):
     """Run a request stream through the library's native serving loop.
     `records` are dicts with "kind" ("render" or "edit"), "arrival" (seconds
     from the start, non-decreasing), "cam" (a camera record, renders) and
-    "edit" ((x0, y0, cells), edits).  Returns a numpy structured array of
-    (admitted, done, version, batch), one row per record."""
+    "edit" ((x0, y0, cells), edits).  `outputs`, optional, gives per record a
+    dict of device tensors for a render's image (None: the loop's own pool,
+    image dropped).  Returns a numpy structured array of (admitted, done,
+    version, batch), one row per record."""
     n = len(records)
     reqs = (hf_request * n)()
     keep = []  # the edit cells stay alive through the call
@@ -499,6 +501,8 @@ def hf_serve_replay(ctx, records, lanes=8, max_batch=8, output_budget=4 << 30, f
             q.kind = HF_REQ_RENDER
             c = camera_records(np.array([rec["cam"]]))
             ctypes.memmove(ctypes.addressof(q.cam), c.ctypes.data, ctypes.sizeof(hf_camera))
+            if outputs is not None and outputs[i] is not None:
+                q.outs = _outputs_array([outputs[i]])[0]
     res = (hf_request_result * n)()
     opts = hf_serve_opts(lanes, max_batch, output_budget, flags, tile_w, tile_h, mip_start)
     _check(lib.hf_serve_replay(ctx, ctypes.cast(reqs, _P) if n else None, n, ctypes.byref(opts),

@@ -55,6 +55,15 @@ uint64_t batch_bytes(uint64_t px, bool shadows) {
     return px * bytes_per_ray(shadows ? HF_SHADOWS : 0) + n * 255;
 }
 
+bool own_outputs(const hf_outputs &o) {
+    return o.hit_cell || o.layer || o.face || o.depth || o.rgba || o.shadow;
+}
+
+// pool bytes a render request takes (none when it brings its own buffers)
+uint64_t pool_bytes(const hf_request &r, bool shadows) {
+    return own_outputs(r.outs) ? 0 : batch_bytes((uint64_t)r.cam.w * r.cam.h, shadows);
+}
+
 }  // namespace
 
 extern "C" int hf_serve_replay(hf_ctx *ctx, const hf_request *reqs, uint32_t n,
@@ -69,8 +78,7 @@ extern "C" int hf_serve_replay(hf_ctx *ctx, const hf_request *reqs, uint32_t n,
         const hf_request &r = reqs[i];
         if (r.kind != HF_REQ_RENDER && r.kind != HF_REQ_EDIT) return HF_E_INVALID_ARG;
         if (i && r.arrival < reqs[i - 1].arrival) return HF_E_INVALID_ARG;
-        if (r.kind == HF_REQ_RENDER &&
-            batch_bytes((uint64_t)r.cam.w * r.cam.h, shadows) > o.output_budget)
+        if (r.kind == HF_REQ_RENDER && pool_bytes(r, shadows) > o.output_budget)
             return HF_E_INVALID_ARG;
     }
     if (n == 0) return HF_OK;
@@ -151,7 +159,7 @@ extern "C" int hf_serve_replay(hf_ctx *ctx, const hf_request *reqs, uint32_t n,
         float ms = 0.0f;
         if (cudaEventElapsedTime(&ms, ref, l.done) != cudaSuccess && err == HF_OK) err = HF_E_CUDA;
         for (uint32_t i : l.reqs) results[i].done = ms / 1e3;
-        cudaFreeAsync(l.block, l.stream);
+        if (l.block) cudaFreeAsync(l.block, l.stream);
         l.block = nullptr;
         mem_used -= l.bytes;
         l.bytes = 0;
@@ -190,7 +198,7 @@ extern "C" int hf_serve_replay(hf_ctx *ctx, const hf_request *reqs, uint32_t n,
             while (!queue.empty() && idx.size() < o.max_batch &&
                    reqs[queue.front()].kind == HF_REQ_RENDER) {
                 const hf_request &r = reqs[queue.front()];
-                const uint64_t b = batch_bytes((uint64_t)r.cam.w * r.cam.h, shadows);
+                const uint64_t b = pool_bytes(r, shadows);
                 if (mem_used + bytes + b > o.output_budget) break;
                 bytes += b;
                 idx.push_back(queue.front());
@@ -200,15 +208,19 @@ extern "C" int hf_serve_replay(hf_ctx *ctx, const hf_request *reqs, uint32_t n,
             if (!idx.empty()) {
                 Lane &l = *free_lane;
                 void *block = nullptr;
-                if (cudaMallocFromPoolAsync(&block, bytes, pool, l.stream) != cudaSuccess) {
+                if (bytes && cudaMallocFromPoolAsync(&block, bytes, pool, l.stream) != cudaSuccess) {
                     err = HF_E_OOM;
                     break;
                 }
                 outs.assign(idx.size(), hf_outputs{});
                 uint64_t off = 0;
-                for (size_t k = 0; k < idx.size(); ++k)
-                    carve(static_cast<char *>(block), off,
-                          (uint64_t)cams[k].w * cams[k].h, shadows, outs[k]);
+                for (size_t k = 0; k < idx.size(); ++k) {
+                    if (own_outputs(reqs[idx[k]].outs))
+                        outs[k] = reqs[idx[k]].outs;
+                    else
+                        carve(static_cast<char *>(block), off, (uint64_t)cams[k].w * cams[k].h,
+                              shadows, outs[k]);
+                }
                 const double ta = now();
                 for (uint32_t i : idx) {
                     results[i].admitted = ta;

@@ -149,7 +149,7 @@ def test_struct_layouts_match_the_header(hf, tmp_path):
         pytest.skip("no C compiler")
     fields = {"hf_camera": ("origin", "w"), "hf_outputs": ("hit_cell", "shadow"),
               "hf_render_opts": ("tile_w", "cuda_stream"),
-              "hf_request": ("arrival", "cam", "x0", "cells"),
+              "hf_request": ("arrival", "cam", "x0", "cells", "outs"),
               "hf_request_result": ("done", "batch"),
               "hf_serve_opts": ("output_budget", "mip_start")}
     lines = []

@@ -135,3 +135,52 @@ def test_native_loop_arguments_are_checked(hf):
         assert (res["done"] > 0).all()
     finally:
         hf.hf_destroy(ctx)
+
+
+def test_native_loop_results_same_alone_and_in_the_mix(hf):
+    """Renders served by hf_serve_replay into the caller's buffers equal, bit
+    for bit, each request rendered alone on a fresh world holding exactly the
+    edits that came before it in the stream."""
+    import torch
+
+    cells, _ = synth.make_grid(512, 512, seed=17, slab_frac=0.3, n_walls=20)
+    records = synth.poisson_requests(cells, 60, rate=2e4, seed=9, edit_every=7,
+                                     resolutions=((160, 90), (320, 180), (96, 64), (640, 360)))
+    outs = [None if r["kind"] == "edit" else hf.alloc_outputs(np.array([r["cam"]]))[0]
+            for r in records]
+    ctx = hf.hf_create(cells)
+    try:
+        res = hf.hf_serve_replay(ctx, records, lanes=4, max_batch=3, output_budget=64 << 20,
+                                 outputs=outs)
+        hf.hf_sync(ctx)
+        torch.cuda.synchronize()
+    finally:
+        hf.hf_destroy(ctx)
+    assert len(set(res["batch"][res["batch"] != 0xFFFFFFFF])) > 3
+    world = cells.copy()
+    checked = 0
+    k = 0
+    while k < len(records):
+        j = k
+        while j < len(records) and records[j]["kind"] == "render":
+            j += 1
+        if j > k:  # renders k..j-1 see the same world
+            cams = np.array([records[i]["cam"] for i in range(k, j)])
+            fresh = hf.hf_create(world)
+            try:
+                alone = [hf.alloc_outputs(cams[q:q + 1])[0] for q in range(len(cams))]
+                for q in range(len(cams)):
+                    hf.hf_render(fresh, cams[q:q + 1], [alone[q]])
+                hf.hf_sync(fresh)
+                torch.cuda.synchronize()
+                for q, i in enumerate(range(k, j)):
+                    for f, t in outs[i].items():
+                        assert torch.equal(t, alone[q][f]), (i, f)
+                    checked += 1
+            finally:
+                hf.hf_destroy(fresh)
+        if j < len(records):  # the edit at j
+            x0, y0, blk = records[j]["edit"]
+            world[y0:y0 + blk.shape[0], x0:x0 + blk.shape[1]] = blk
+        k = j + 1
+    assert checked == sum(r["kind"] == "render" for r in records)
