@@ -305,7 +305,13 @@ def hf_render(ctx, cams, outs, opts=None):
 
     cams: CAMERA_DTYPE array (or records with the same fields); outs: a list
     of dicts keyed by hit_cell, layer, face, depth, rgba, shadow (missing or
-    None entries are not written); opts: an hf_render_opts or None."""
+    None entries are not written); opts: an hf_render_opts or None.
+
+    The render is asynchronous on the context's stream (or opts.cuda_stream):
+    keep the output tensors alive until it has completed there (hf_sync, or
+    an event on that stream).  torch's caching allocator does not see that
+    stream, so a tensor freed early could be handed out again while the
+    kernel still writes it."""
     recs = camera_records(cams)
     n = len(recs)
     if len(outs) != n:
