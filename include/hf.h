@@ -9,8 +9,9 @@
  * point along it is reported; a bounded rectangular edit must be visible on the
  * next render without a rebuild (Sections 2 and 4.4).  The library answers
  * this exactly with fixed-point integer arithmetic, skipping empty space with a
- * conservative min/max pyramid (the "skip only known-empty space" rule of the
- * hierarchy in Section 3.2) that an edit repairs incrementally.
+ * conservative min/max pyramid (the hierarchy of Section 3.2 may pass over a
+ * region only when it is known to hold nothing) that an edit repairs
+ * incrementally.
  *
  * Units.  One world unit is one cell width and one height step.  Positions are
  * fixed point in units of 2^-16 world units.  A pixel ray is p(t) = O + t d,

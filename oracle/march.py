@@ -8,9 +8,9 @@ d = integer direction / 2^16, so t is the same parameter as the exact cast's):
   * the segment [0, t_end] is clipped at the far distance (t_far = far / |d|)
     and, for a descending ray, at z = 0 (t_z = -o_z / d_z);
   * `steps` samples at t_i = i * (t_end / (steps + 1)), i = 1..steps, spaced
-    uniformly over the clipped segment (the text's "sampled uniformly"; the
-    listing's update of `a` inside the loop would space them geometrically
-    and never reach the far part, so the text is taken);
+    uniformly over the clipped segment (as the text describes; the listing
+    moves the lower bound inside its loop, which would space them
+    geometrically and never reach the far part, so the text is taken);
   * the first sample whose point is SOLID stops the search: z <= low, or
     mid <= z <= high, for the cell containing the point's x, y (floor; no
     solid outside the grid);

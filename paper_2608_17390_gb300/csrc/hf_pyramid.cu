@@ -5,8 +5,8 @@
 // (slab ? h1 : 255), byte2 = max over cells of (slab ? h2 : h0).  A node is
 // the per-byte max/min of its (up to four) children, so after an edit of a cell
 // rectangle only the nodes over that rectangle change, level by level: the
-// "rebuild affected cells and their ancestors" of the paper's Sections 2 and
-// 3.2, applied to a 2.5-D min/max hierarchy.  The full build (hf_create,
+// incremental repair of the paper's Sections 2 and 3.2 (the edited cells, then
+// the nodes above them), applied to a 2.5-D min/max hierarchy.  The full build (hf_create,
 // hf_rebuild) makes levels 1..6 per 64 x 64 tile in shared memory so the cells
 // are read from HBM once; repair recomputes the nodes over a rectangle level by
 // level.  The two paths share only the byte-wise combine, and the tests compare
