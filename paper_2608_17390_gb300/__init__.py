@@ -491,6 +491,8 @@ def hf_serve_replay(ctx, records, lanes=8, max_batch=8, output_budget=4 << 30, f
     image dropped).  Returns a numpy structured array of (admitted, done,
     version, batch), one row per record."""
     n = len(records)
+    if outputs is not None and len(outputs) != n:
+        raise ValueError("one output entry (or None) per record")
     reqs = (hf_request * n)()
     keep = []  # the edit cells stay alive through the call
     for i, rec in enumerate(records):

@@ -174,6 +174,8 @@ def test_struct_layouts_match_the_header(hf, tmp_path):
 def test_serve_replay_rejects_before_touching_the_gpu(hf):
     opts = hf.hf_serve_opts(8, 8, 1 << 30, 0, 0, 0, hf.HF_MIP_AUTO)
     assert hf.lib.hf_serve_replay(None, None, 0, ctypes.byref(opts), None) == hf.HF_E_INVALID_ARG
+    with pytest.raises(ValueError):
+        hf.hf_serve_replay(None, [{"kind": "render", "arrival": 0.0}], outputs=[])
 
 
 def test_pair_validation_agrees_with_the_oracle(hf):
