@@ -8,15 +8,28 @@
   paper states ("a sample interval can still skip a thinner feature") -- and
   found by every ray once the spacing is below one cell.
 * Misses stay misses: no hit is made at the ground plane or outside the grid.
+* A ray whose samples and bisection midpoints are exact in float32 pins the
+  spacing t_end / (steps + 1), the clip at z = 0, the number of bisections
+  and which end of the bracket they keep.
 """
 
+import importlib.util
 import math
+import os
 
 import numpy as np
 
 import oracle
 import synth
-from oracle import march
+
+if os.environ.get("HF_MARCH_ORACLE"):
+    # a planted-mistake copy of the march oracle (tests/test_oracle_mutations.py)
+    _spec = importlib.util.spec_from_file_location("oracle._march_mutant",
+                                                   os.environ["HF_MARCH_ORACLE"])
+    march = importlib.util.module_from_spec(_spec)
+    _spec.loader.exec_module(march)
+else:
+    from oracle import march
 
 S = 65536
 
@@ -53,6 +66,57 @@ def test_flat_plane_hits_inside_the_bisection_bracket():
             assert t_star * n * (1 - 1e-5) <= depth <= (t_star + dt / 16) * n * (1 + 1e-5) + 1e-4
             checked += 1
     assert checked > 1000
+
+
+def test_sample_spacing_and_bisection_closed_form():
+    """One ray whose every sample and bisection midpoint is exact in float32.
+
+    Origin height 129, direction (1, 0, -1) world units per unit t, floor of
+    height 1 everywhere, far 600: the segment is clipped at z = 0, so
+    t_end = 129 and the spacing t_end / (steps + 1) is exactly 1.  Samples
+    t = 1 .. 128 lie at heights 128 .. 1; the first solid one is t = 128
+    (z = 1, closed floor).  The four bisections of [127, 128] try 127.5,
+    127.75, 127.875 and 127.9375, all above the floor, so the solid end stays
+    at t = 128: depth = 128 * float32(sqrt 2), hit cell x = 10 + 128.  Any
+    other spacing, clip or kept end moves the depth off this value."""
+    W, H = 200, 4
+    cells = _flat(W, H, 1)
+    o = np.array([[10 * S + S // 2, 2 * S, 129 * S]], np.int64)
+    d = np.array([[S, 0, -S]], np.int64)
+    r = march.march(cells, o, d, steps=128, far=600.0, bisections=4)
+    assert int(r["hit_cell"][0]) == 2 * W + 138
+    assert int(r["layer"][0]) == 0
+    assert float(r["depth"][0]) == float(np.float32(128.0) * np.sqrt(np.float32(2.0)))
+    # three bisections leave [127.875, 128]: the solid end is still 128
+    r3 = march.march(cells, o, d, steps=128, far=600.0, bisections=3)
+    assert float(r3["depth"][0]) == float(r["depth"][0])
+    # a floor of height 2: first solid sample t = 127 (z = 2); the midpoints
+    # 126.5, 126.75, 126.875, 126.9375 lie above it
+    r2 = march.march(_flat(W, H, 2), o, d, steps=128, far=600.0, bisections=4)
+    assert float(r2["depth"][0]) == float(np.float32(127.0) * np.sqrt(np.float32(2.0)))
+
+
+def test_bisection_converges_on_the_crossing():
+    """Origin height 100.5 over a floor of height 1, same direction: t_end =
+    100.5, spacing 100.5 / 129 (not exact), and the crossing z = 1 lies at
+    t* = 99.5, between samples 127 and 128.  b bisections leave the solid end
+    within spacing / 2^b after t*, and more bisections never move it away
+    from t* or before it."""
+    W, H = 200, 4
+    cells = _flat(W, H, 1)
+    o = np.array([[10 * S + S // 2, 2 * S, 100 * S + S // 2]], np.int64)
+    d = np.array([[S, 0, -S]], np.int64)
+    n = math.sqrt(2.0)
+    dt = 100.5 / 129
+    prev = None
+    for b in (0, 1, 2, 4, 8):
+        r = march.march(cells, o, d, bisections=b)
+        depth = float(r["depth"][0])
+        assert int(r["hit_cell"][0]) == 2 * W + 110  # x = 10.5 + t, t in [99.5, 100.28]
+        assert 99.5 * n * (1 - 1e-6) <= depth <= (99.5 + dt / (1 << b)) * n * (1 + 1e-6), b
+        if prev is not None:
+            assert depth <= prev
+        prev = depth
 
 
 def test_thin_wall_is_skipped_at_128_steps_and_found_with_fine_steps():

@@ -6,6 +6,8 @@
   ties are frequent;
 * closed forms written here with exact fractions: a flat plane, one floating
   slab box over a flat floor, a vertical wall, and a wall's shadow;
+* hand-derived colours for every face of a cell, lit, turned away from the
+  sun and occluded (tests/golden/shading_faces.json);
 * the pyramid against a second implementation and against the parent/child
   recurrence.
 """
@@ -336,6 +338,38 @@ def test_closed_form_wall_shadow():
         assert int(r["shadow"][k]) == exp, (p, ent)
         shadowed += exp
     assert 10 < shadowed < len(o) - 10
+
+
+def _shading_fixture():
+    with open(os.path.join(HERE, "golden", "shading_faces.json")) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("case", _shading_fixture()["cases"], ids=lambda c: c["name"])
+def test_shading_per_face(case):
+    """One hand-derived colour per face of the cell, lit, turned away from
+    the sun and occluded (tests/golden/shading_faces.json): pins the sign and
+    axis of N.L for every face, the ambient and diffuse weights, the shadow
+    factor and the rounding."""
+    fx = _shading_fixture()
+    W = H = 16
+    h0 = np.full((H, W), 2, np.int64)
+    h1 = np.zeros((H, W), np.int64)
+    h2 = np.zeros((H, W), np.int64)
+    mat = np.zeros((H, W), np.int64)
+    for x0, x1, y0, y1, a, b, c, m in fx["scenes"][case["scene"]]:
+        h0[y0:y1, x0:x1], h1[y0:y1, x0:x1], h2[y0:y1, x0:x1], mat[y0:y1, x0:x1] = a, b, c, m
+    cells = synth.pack_cells(h0, h1, h2, mat)
+    o = np.array([[round(v * S) for v in case["origin"]]], np.int64)
+    d = np.array([case["dir"]], np.int64)
+    r = oracle.trace_rays(cells, o, d, shadows=True, sun=tuple(fx["suns"][case["sun"]]))
+    e = case["expect"]
+    assert int(r["hit_cell"][0]) == e["y"] * W + e["x"]
+    assert (int(r["layer"][0]), int(r["face"][0])) == (e["layer"], e["face"])
+    assert float(r["depth"][0]) == pytest.approx(e["depth"], rel=1e-12)
+    assert int(r["shadow"][0]) == e["shadow"]
+    rgba = int(r["rgba"][0])
+    assert [rgba & 0xFF, (rgba >> 8) & 0xFF, (rgba >> 16) & 0xFF, rgba >> 24] == e["rgb"] + [255]
 
 
 def test_shading_invariants():
