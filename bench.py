@@ -227,29 +227,69 @@ class Clocks:
 
 # --------------------------------------------------------------- CPU oracle
 
-def cpu_oracle_sample(wl, budget_s=15.0, seed=0):
-    """Oracle rays/s on a bounded, seeded sample of the workload's pixels."""
+def cpu_model():
+    """The host CPU's model name (lscpu), or None."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
+def _pixel_sample(cams, frac, seed):
+    """Seeded pixel indices per camera: about frac of each camera's pixels (at
+    least 16), so the sample mixes views, resolutions and ray lengths as the
+    whole workload does."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for c in cams:
+        n = int(c["w"]) * int(c["h"])
+        k = max(16, min(n, int(round(frac * n))))
+        out.append(np.unique(rng.integers(0, n, k)).astype(np.uint32))
+    return out
+
+
+def cpu_oracle_sample(wl, budget_s=15.0, seed=0, threads=None):
+    """Oracle rays/s on a bounded, seeded sample of the workload: the same
+    fraction of every camera's pixels, one oracle call per camera on
+    `threads` host threads (all cores by default).  A short calibration pass
+    picks the fraction so that the measured pass takes about budget_s."""
     import oracle
 
-    cores = os.cpu_count() or 1
+    cores = threads or os.cpu_count() or 1
     cams = wl["cams"]
-    rng = np.random.default_rng(seed)
-    per = 64
-    t0 = time.perf_counter()
-    done = 0
-    rounds = 0
-    while time.perf_counter() - t0 < budget_s and rounds < 64:
-        for c in cams:
-            n = int(c["w"]) * int(c["h"])
-            pix = np.sort(rng.integers(0, n, per)).astype(np.uint32)
-            oracle.render(wl["cells"], c, shadows=wl["shadows"], pix=pix, nthreads=cores)
-            done += per
-        rounds += 1
-        per = min(per * 2, 4096)
-    dt = time.perf_counter() - t0
+    total = n_rays(cams)
+
+    def run(frac, sd):
+        pix = _pixel_sample(cams, frac, sd)
+        t0 = time.perf_counter()
+        for c, p in zip(cams, pix):
+            oracle.render(wl["cells"], c, shadows=wl["shadows"], pix=p, nthreads=cores)
+        return sum(len(p) for p in pix), time.perf_counter() - t0
+
+    n0, t0 = run(min(1.0, 2.0e4 * cores / total), seed + 7919)
+    frac = min(1.0, budget_s * (n0 / t0) / total)
+    done, dt = run(frac, seed)
     return {"value": done / dt, "unit": "primary rays/s", "cores": cores, "kind": "oracle",
-            "sample": "%d seeded pixels spread over all %d cameras of the workload%s, %.1f s"
-                      % (done, len(cams), " with shadow rays" if wl["shadows"] else "", dt)}
+            "sample": "%d seeded pixels (%.3g%% of each of the %d cameras' pixels, one oracle "
+                      "call per camera)%s, %.1f s" % (done, 100 * frac, len(cams),
+                                                     " with shadow rays" if wl["shadows"] else "",
+                                                     dt)}
+
+
+def cpu_baseline(wl, budget_s=15.0):
+    """The host-core oracle figure for the bench line: all cores, plus the
+    same sample design on one core (a third of the budget), with the CPU
+    model and core count."""
+    allc = cpu_oracle_sample(wl, budget_s=budget_s)
+    one = cpu_oracle_sample(wl, budget_s=budget_s / 3.0, seed=1, threads=1)
+    allc["single_core"] = {"value": one["value"], "unit": one["unit"], "sample": one["sample"]}
+    allc["nproc"] = os.cpu_count()
+    allc["cpu_model"] = cpu_model()
+    return allc
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -306,10 +346,10 @@ def run_hf(args):
         opts = hf.make_opts(flags=flags, mip_start=args.mip, tile_w=args.tile_w,
                             tile_h=args.tile_h)
     tile_w, tile_h, mip_start = opts.tile_w or 8, opts.tile_h or 4, opts.mip_start
-    rng = np.random.default_rng(1234 + rank)
+    rng = np.random.default_rng(1234)
     H, W = cells.shape
 
-    def do_edit():
+    def draw_edit():
         cx, cy = int(rng.integers(0, W)), int(rng.integers(0, H))
         x0, y0, blk = synth.crater_edit(cells, cx, cy)
         if "texels" in wl:  # a paired-texel world is edited in whole, representable pairs
@@ -318,6 +358,18 @@ def run_hf(args):
             full = cells[y0:y0 + h, xa:xb].copy()
             full[:, x0 - xa:x0 - xa + w] = blk
             x0, blk = xa, synth.pairify(full)
+        return x0, y0, blk
+
+    def do_edit():
+        if ws > 1:
+            # the replicas' one exchange step: rank 0 draws the crater, every
+            # rank receives it and applies it to its own world
+            from paper_2608_17390_gb300.replicas import replicated_edit
+
+            replicated_edit(draw_edit() if rank == 0 else None, cells, src=0, device="cuda",
+                            apply=lambda x0, y0, b: hf.hf_edit(ctx, x0, y0, b))
+            return
+        x0, y0, blk = draw_edit()
         hf.hf_edit(ctx, x0, y0, blk)
         cells[y0:y0 + blk.shape[0], x0:x0 + blk.shape[1]] = blk
 
@@ -517,7 +569,7 @@ def run_hf(args):
         "e2e": e2e,
     }
     if not args.no_cpu and ws == 1:  # the host-core oracle sample: rank 0 at N = 1 only
-        line["cpu_baseline"] = cpu_oracle_sample(wl, budget_s=args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_seconds)
     print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
@@ -566,23 +618,32 @@ def run_serve(args):
     # each load: the library's native loop (hf_serve_replay, reported), then the
     # Python loop over the same request stream (for comparison)
     results, py_results = {}, {}
+    all_clocks = Clocks(torch.cuda.current_device())
+    all_clocks.start()
     for load in (0.7, 1.0):
         records = synth.poisson_requests(cells, args.serve_requests, load * cap_req,
                                          seed=int(load * 100))
+        clocks = Clocks(torch.cuda.current_device())
+        clocks.start()
         t0 = time.perf_counter()
         done = serve.run_native(srv.ctx, records, lanes=SERVE_LANES, max_batch=SERVE_MAX_BATCH,
                                 mem_bytes=4 << 30)
         st = serve.summarize(done, time.perf_counter() - t0)
+        st["clocks"] = clocks.stop()
         st["offered_requests_per_s"] = load * cap_req
         st["batches"] = len({r.batch_id for r in done if r.kind == "render"})
         results["load_%d%%" % int(load * 100)] = st
         b0 = srv.batches
+        clocks = Clocks(torch.cuda.current_device())
+        clocks.start()
         t0 = time.perf_counter()
         done = srv.run(serve.requests_from(records))
         st = serve.summarize(done, time.perf_counter() - t0)
+        st["clocks"] = clocks.stop()
         st["batches"] = srv.batches - b0
         st["max_inflight_batches"] = srv.max_inflight
         py_results["load_%d%%" % int(load * 100)] = st
+    ck = all_clocks.stop()
     srv.close()
     if rank != 0:
         return
@@ -600,7 +661,7 @@ def run_serve(args):
                                    "crater edit every 11th request", "lanes": SERVE_LANES,
                        "output_memory_budget_bytes": 4 << 30, "max_batch": SERVE_MAX_BATCH},
             "capacity_rays_per_s": cap_rays, "capacity_requests_per_s": cap_req,
-            "loads": results, "loads_python_loop": py_results}
+            "loads": results, "loads_python_loop": py_results, "clocks": ck}
     print(json.dumps(line))
 
 
@@ -636,6 +697,8 @@ def run_protocol(args):
         hf.hf_sync(ctx)
         return a.elapsed_time(b) / reps
 
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
     exact = hf.make_opts(stream=stream.cuda_stream)
     frame = lambda r: hf.hf_render(ctx, cams[r % 12:r % 12 + 1], outs[r % 12:r % 12 + 1], exact)
     batch = lambda r: hf.hf_render(ctx, cams, outs, exact)
@@ -706,6 +769,7 @@ def run_protocol(args):
         row["edit_ms"] = ev_ms(lambda r: hf.hf_edit(ctx, x0, y0, blk), 1)
         hf.hf_edit(ctx, x0, y0, cells[y0:y0 + blk.shape[0], x0:x0 + blk.shape[1]].copy())  # undo
         res["voxel_%d%d%d_inner%d" % (v + (inner,))] = row
+    ck = clocks.stop()
     hf.hf_destroy(ctx)
     line = {"metric": "frame time, paper protocol (12 views, 1280x800): exact cast vs the "
                       "paper's fixed-step march, Scattered method and RayVoxel, with Section 4.2 "
@@ -716,7 +780,7 @@ def run_protocol(args):
             "config": {"workload": "2048x16384 grid (seed 4, 30% slabs), 3 views at each pitch "
                                    "0/-30/-60/-90, 1280x800, hfov 75, far 600 (march); "
                                    "steady-state frames, primary rays only"},
-            "results": res}
+            "results": res, "clocks": ck}
     print(json.dumps(line))
 
 
@@ -741,7 +805,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(secs)) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i64",
             "data": "synthetic", "config": {"workload": wl["name"]},
-            "cpu_baseline": dict(last, value=value),
+            "cpu_baseline": dict(last, value=value, nproc=os.cpu_count(), cpu_model=cpu_model()),
             "e2e": {"value": value, "unit": "primary rays/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -750,7 +814,9 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)  # about 1 s timed: several clock samples at 200 ms
+    # default: about 1 s timed on every workload, so the 200 ms clock sampler
+    # sees several samples (50 batched-camera steps; many more single-camera ones)
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hf", choices=["hf", "reference"])
     ap.add_argument("--workload", default="c3",
@@ -769,6 +835,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 20 if args.impl == "reference" else {"c1": 20000, "c2": 8000}.get(
+            args.workload, 50)
     if args.warmup < 3 and args.impl == "hf":
         args.warmup = 3
     if args.impl == "reference":

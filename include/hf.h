@@ -231,9 +231,10 @@ int hf_render(hf_ctx *ctx, const hf_camera *cams, uint32_t n, const hf_outputs *
  * It renders n <= HF_NOALLOC_MAX_CAMERAS cameras with the same kernel and the
  * same results as hf_render, always as one batched launch on the context's
  * own stream (opts->cuda_stream must be NULL or that stream), so edits and
- * renders stay ordered.  Honoured flags: HF_SHADOWS and HF_SYNC (with HF_SYNC
+ * renders stay ordered.  Accepted flags: HF_SHADOWS and HF_SYNC (with HF_SYNC
  * the step-guard status is returned; without it this entry point reports no
- * step-guard status, and hf_sync does not see it).  Other flags are ignored.
+ * step-guard status, and hf_sync does not see it).  Any other flag is refused
+ * with HF_E_INVALID_ARG before anything is enqueued.
  *
  * Scratch: one statically allocated device array of about 28 KiB (batch
  * header with the tile counter, camera table, status word) that every GPU
@@ -246,7 +247,7 @@ int hf_render(hf_ctx *ctx, const hf_camera *cams, uint32_t n, const hf_outputs *
  * camera table is copied from pageable host memory, so the call waits for
  * earlier work on the context's stream before returning.
  * Errors: HF_E_INVALID_ARG (null, n > HF_NOALLOC_MAX_CAMERAS, invalid camera,
- * tile shape or stream), HF_E_CUDA, and with HF_SYNC HF_E_STEP_LIMIT. */
+ * tile shape, stream or flag), HF_E_CUDA, and with HF_SYNC HF_E_STEP_LIMIT. */
 #define HF_NOALLOC_MAX_CAMERAS 256u
 int hf_render_noalloc(hf_ctx *ctx, const hf_camera *cams, uint32_t n, const hf_outputs *outs,
                       const hf_render_opts *opts);
@@ -449,10 +450,14 @@ int hf_stats(hf_ctx *ctx, uint64_t out[5]);
  * renders admitted before it do not see it and every later one does; a batch
  * retires when its completion event has fired, and its output memory (from a
  * pool the loop owns, unless the request names its own buffers) is released.
- * Times are seconds from the start of the replay: `admitted` on the host
- * clock, `done` the device completion of the request's batch (a reference
- * event maps device time to the host clock) or, for an edit, the hf_edit
- * call.  The loop returns when every request is done. */
+ * Times are seconds from the start of the replay on the host clock:
+ * `admitted` when the loop admitted the request (renders) or called hf_edit
+ * (edits); `done` the device completion of the request's batch (renders) or
+ * of the edit's copy and pyramid repair (edits).  Device times are mapped to
+ * the host clock through a reference event whose host time is bracketed, before
+ * the first request, by timed event round trips on an idle stream (the
+ * bracket is a few microseconds wide).  The loop returns when every request
+ * is done. */
 #define HF_REQ_RENDER 0u
 #define HF_REQ_EDIT 1u
 
@@ -470,7 +475,7 @@ typedef struct {
 
 typedef struct {
     double admitted;      /* host time of admission (renders) or of the hf_edit call (edits) */
-    double done;          /* device completion of the batch (renders); the hf_edit call (edits) */
+    double done;          /* device completion of the batch (renders) or of the edit (edits) */
     uint32_t version;     /* edits applied before admission (renders); this edit's number (edits) */
     uint32_t batch;       /* batch index (renders); 0xFFFFFFFF for edits */
 } hf_request_result;

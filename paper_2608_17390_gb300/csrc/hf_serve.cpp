@@ -7,8 +7,16 @@
 // for the renders already issued; a later render waits for the edit) give the
 // version semantics.  Output memory comes from a stream-ordered pool the call
 // owns; a batch's block is released when its completion event has fired.
+//
+// Clocks: arrivals and admissions are host times; completions are CUDA events.
+// A reference event, then a few timed round trips (host time before an event
+// is recorded on an idle stream, host time after it has fired) bracket the
+// host time of the reference event; device times are mapped to the host clock
+// through the middle of that bracket, so frame and edit-to-visible latencies
+// subtract times on one clock.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cstring>
 #include <deque>
@@ -16,6 +24,7 @@
 #include <vector>
 
 #include "hf.h"
+#include "hf_internal.h"
 
 namespace {
 
@@ -91,7 +100,16 @@ extern "C" int hf_serve_replay(hf_ctx *ctx, const hf_request *reqs, uint32_t n,
     std::vector<Lane> lanes(o.lanes);
     cudaMemPool_t pool = nullptr;
     cudaEvent_t ref = nullptr;
+    hf::CtxView view;
+    if (hf::ctx_view(ctx, &view)) return HF_E_INVALID_ARG;
+    // completion events of applied edits (recorded on the context's stream,
+    // where hf_edit enqueues its copy and pyramid repair), created on demand
+    std::vector<cudaEvent_t> edit_ev;
+    std::vector<uint32_t> edit_req;
+    size_t edit_retired = 0;
     auto cleanup = [&]() {
+        for (cudaEvent_t e : edit_ev)
+            if (e) cudaEventDestroy(e);
         for (auto &l : lanes) {
             if (l.stream) cudaStreamSynchronize(l.stream);
             if (l.block) cudaFreeAsync(l.block, l.stream);
@@ -132,6 +150,35 @@ extern "C" int hf_serve_replay(hf_ctx *ctx, const hf_request *reqs, uint32_t n,
     using clock = std::chrono::steady_clock;
     const clock::time_point t0 = clock::now();
     auto now = [&]() { return std::chrono::duration<double>(clock::now() - t0).count(); };
+    // host time of the reference event: each round trip gives
+    // before <= dev + shift <= after for the event's device time dev
+    double shift = 0.0;
+    {
+        cudaEvent_t cal = nullptr;
+        double lo = -1e30, hi = 1e30, best = 1e30, best_mid = 0.0;
+        bool ok = cudaEventCreate(&cal) == cudaSuccess;
+        for (int k = 0; ok && k < 8; ++k) {
+            const double before = now();
+            ok = cudaEventRecord(cal, lanes[0].stream) == cudaSuccess &&
+                 cudaEventSynchronize(cal) == cudaSuccess;
+            const double after = now();
+            float ms = 0.0f;
+            ok = ok && cudaEventElapsedTime(&ms, ref, cal) == cudaSuccess;
+            const double dev = ms / 1e3;
+            lo = std::max(lo, before - dev);
+            hi = std::min(hi, after - dev);
+            if (after - before < best) {
+                best = after - before;
+                best_mid = 0.5 * (before + after) - dev;
+            }
+        }
+        if (cal) cudaEventDestroy(cal);
+        if (!ok) {
+            cleanup();
+            return HF_E_CUDA;
+        }
+        shift = lo <= hi ? 0.5 * (lo + hi) : best_mid;
+    }
 
     hf_render_opts ro;
     std::memset(&ro, 0, sizeof(ro));
@@ -158,7 +205,7 @@ extern "C" int hf_serve_replay(hf_ctx *ctx, const hf_request *reqs, uint32_t n,
         }
         float ms = 0.0f;
         if (cudaEventElapsedTime(&ms, ref, l.done) != cudaSuccess && err == HF_OK) err = HF_E_CUDA;
-        for (uint32_t i : l.reqs) results[i].done = ms / 1e3;
+        for (uint32_t i : l.reqs) results[i].done = ms / 1e3 + shift;
         if (l.block) cudaFreeAsync(l.block, l.stream);
         l.block = nullptr;
         mem_used -= l.bytes;
@@ -168,10 +215,29 @@ extern "C" int hf_serve_replay(hf_ctx *ctx, const hf_request *reqs, uint32_t n,
         return true;
     };
 
+    // edits complete in order on the context's stream
+    auto retire_edits = [&](bool block) {
+        while (edit_retired < edit_ev.size()) {
+            cudaEvent_t e = edit_ev[edit_retired];
+            if (block) {
+                if (cudaEventSynchronize(e) != cudaSuccess && err == HF_OK) err = HF_E_CUDA;
+            } else {
+                const cudaError_t q = cudaEventQuery(e);
+                if (q == cudaErrorNotReady) return;
+                if (q != cudaSuccess && err == HF_OK) err = HF_E_CUDA;
+            }
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, ref, e) != cudaSuccess && err == HF_OK) err = HF_E_CUDA;
+            results[edit_req[edit_retired]].done = ms / 1e3 + shift;
+            ++edit_retired;
+        }
+    };
+
     while (err == HF_OK && (next < n || !queue.empty())) {
         const double t = now();
         while (next < n && reqs[next].arrival <= t) queue.push_back(next++);
         for (auto &l : lanes) retire(l, false);
+        retire_edits(false);
         // edits at the head of the queue, in order
         while (err == HF_OK && !queue.empty() && reqs[queue.front()].kind == HF_REQ_EDIT) {
             const uint32_t i = queue.front();
@@ -181,8 +247,16 @@ extern "C" int hf_serve_replay(hf_ctx *ctx, const hf_request *reqs, uint32_t n,
             const int e = hf_edit(ctx, r.x0, r.y0, r.w, r.h, r.cells, r.w);
             if (e != HF_OK) err = e;
             results[i].version = ++version;
-            results[i].done = results[i].admitted;
+            results[i].done = results[i].admitted;  // replaced when its event fires
             results[i].batch = 0xFFFFFFFFu;
+            cudaEvent_t ev = nullptr;
+            if (err == HF_OK && (cudaEventCreate(&ev) != cudaSuccess ||
+                                 cudaEventRecord(ev, (cudaStream_t)view.stream) != cudaSuccess))
+                err = HF_E_CUDA;
+            if (ev) {
+                edit_ev.push_back(ev);
+                edit_req.push_back(i);
+            }
         }
         // one batch of renders on a free lane
         Lane *free_lane = nullptr;
@@ -244,6 +318,7 @@ extern "C" int hf_serve_replay(hf_ctx *ctx, const hf_request *reqs, uint32_t n,
         if (queue.empty() || !free_lane) std::this_thread::yield();
     }
     for (auto &l : lanes) retire(l, true);
+    retire_edits(true);
     const int sync = hf_sync(ctx);
     cleanup();
     if (err != HF_OK) return err;

@@ -716,6 +716,9 @@ extern "C" int hf_render_noalloc(hf_ctx *ctx, const hf_camera *cams, uint32_t n,
     o.mip_start = HF_MIP_AUTO;
     if (opts) o = *opts;
     if (o.cuda_stream && o.cuda_stream != v.stream) return HF_E_INVALID_ARG;
+    // a flag this entry point cannot honour (host outputs, statistics, plain
+    // or graph launches, admission) is refused, not silently dropped
+    if (o.flags & ~(HF_SHADOWS | HF_SYNC)) return HF_E_INVALID_ARG;
     const uint32_t tw = o.tile_w ? o.tile_w : 8, th = o.tile_h ? o.tile_h : 4;
     const int twl = ilog2_pow2(tw), thl = ilog2_pow2(th);
     if (twl < 0 || thl < 0 || tw * th < 32 || tw * th > 256 || tw > 256 || th > 256)

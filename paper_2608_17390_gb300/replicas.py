@@ -44,3 +44,31 @@ def broadcast_edit(edit, src=0, device=None):
         cells.copy_(torch.from_numpy(blk.reshape(-1).view(np.int32)))
     dist.broadcast(cells, src)
     return x0, y0, cells.cpu().numpy().view(np.uint32).reshape(h, w)
+
+
+def replicated_edit(edit, cells, src=0, device=None, apply=None):
+    """One edit of the replicated world: the exchange step of the multi-GPU
+    path.
+
+    Rank `src` passes edit = (x0, y0, block) and the others None.  The edit is
+    broadcast (broadcast_edit); then every rank checks it the way hf_edit does
+    on the host before any device work -- the rectangle inside its grid
+    (HF_E_OUT_OF_BOUNDS) and every cell a valid two-interval word
+    (hf_validate_cells, HF_E_INVALID_ARG) -- so that a bad edit raises the same
+    HFError on every rank and no replica applies it.  A valid edit is passed to
+    `apply(x0, y0, block)` (hf_edit on the rank's context; None for host-only
+    use) and written into the rank's host mirror `cells`.  Returns the edit."""
+    from . import HF_E_OUT_OF_BOUNDS, HF_OK, HFError, hf_validate_cells
+
+    x0, y0, blk = broadcast_edit(edit, src=src, device=device)
+    H, W = cells.shape
+    h, w = blk.shape
+    if w == 0 or h == 0 or x0 < 0 or y0 < 0 or x0 + w > W or y0 + h > H:
+        raise HFError(HF_E_OUT_OF_BOUNDS, "replicated_edit")
+    rc, _ = hf_validate_cells(blk)
+    if rc != HF_OK:
+        raise HFError(rc, "replicated_edit")
+    if apply is not None:
+        apply(x0, y0, blk)
+    cells[y0:y0 + h, x0:x0 + w] = blk
+    return x0, y0, blk

@@ -110,6 +110,8 @@ class Server:
         ref.record(self.main)
         ref.synchronize()
         t0 = time.perf_counter()
+        shift = clock_shift(torch, ref, self.lanes[0], lambda: time.perf_counter() - t0)
+        edit_events = []
         pending = collections.deque(requests)
         queue = collections.deque()
         completed = []
@@ -120,7 +122,7 @@ class Server:
                 ev.synchronize()
             elif not ev.query():
                 return False
-            t_done = ref.elapsed_time(ev) / 1e3
+            t_done = ref.elapsed_time(ev) / 1e3 + shift
             for r in batch:
                 r.done = t_done
                 self.mem_used -= self.bytes_for(r)
@@ -144,10 +146,13 @@ class Server:
                 x0, y0, blk = r.edit
                 r.call_time = time.perf_counter() - t0
                 hf_edit(self.ctx, x0, y0, blk)
+                ev = torch.cuda.Event(enable_timing=True)
+                ev.record(self.main)  # after the edit's copy and repair
+                edit_events.append((r, ev))
                 self.version += 1
                 r.version = self.version
                 r.admitted = r.call_time
-                r.done = r.call_time
+                r.done = r.call_time  # replaced by the device completion below
                 completed.append(r)
             free = [i for i in range(len(self.lanes)) if self.busy[i] is None]
             if queue and free:
@@ -175,7 +180,30 @@ class Server:
         for i in range(len(self.lanes)):
             if self.busy[i] is not None:
                 retire(i, block=True)
+        for r, ev in edit_events:
+            ev.synchronize()
+            r.done = ref.elapsed_time(ev) / 1e3 + shift
         return completed
+
+
+def clock_shift(torch, ref, stream, now, rounds=8):
+    """Host time (seconds, on the clock `now`) of the CUDA event `ref`, which
+    has already fired: each round trip records an event on the idle `stream`
+    between two host readings, so before <= dev + shift <= after for its
+    device time dev after `ref`.  Returns the middle of the intersected
+    bracket (or of the narrowest round trip, if the brackets disagree)."""
+    lo, hi, best = -1e30, 1e30, None
+    ev = torch.cuda.Event(enable_timing=True)
+    for _ in range(rounds):
+        before = now()
+        ev.record(stream)
+        ev.synchronize()
+        after = now()
+        dev = ref.elapsed_time(ev) / 1e3
+        lo, hi = max(lo, before - dev), min(hi, after - dev)
+        if best is None or after - before < best[0]:
+            best = (after - before, 0.5 * (before + after) - dev)
+    return 0.5 * (lo + hi) if lo <= hi else best[1]
 
 
 def run_native(ctx, records, lanes=8, max_batch=8, mem_bytes=4 << 30, shadows=False, opts=None):

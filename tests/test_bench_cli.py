@@ -6,6 +6,7 @@ import os
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -81,3 +82,24 @@ def test_alu_roofline_only_for_the_profiled_launch():
             t2, m2 = key.split("@")[1].split("/")
             r2 = bench._alu_roofline("c3", 188006400, 30.0, t2, int(m2), 152, 2070.0)
             assert r2["warp_instructions_per_primary_ray"] == pytest.approx(float(v))
+
+
+def test_cpu_baseline_samples_every_camera_in_proportion():
+    """The host-core oracle figure samples the same fraction of every
+    camera's pixels (the workload's own mix), calls the oracle once per
+    camera, and reports an all-core and a single-core rate with the CPU."""
+    import bench
+
+    wl = bench.workload("c3", scale=16)
+    cams = wl["cams"]
+    pix = bench._pixel_sample(cams, 0.05, seed=3)
+    assert len(pix) == len(cams)
+    for c, p in zip(cams, pix):
+        n = int(c["w"]) * int(c["h"])
+        assert (np.diff(p.astype(np.int64)) > 0).all() and p.max() < n
+        assert abs(len(p) - 0.05 * n) <= 0.05 * 0.05 * n + 16
+    wl1 = bench.workload("c1")
+    b = bench.cpu_baseline(wl1, budget_s=0.3)
+    assert b["kind"] == "oracle" and b["value"] > 0 and b["cores"] == os.cpu_count()
+    assert b["single_core"]["value"] > 0 and b["nproc"] == os.cpu_count()
+    assert "cpu_model" in b

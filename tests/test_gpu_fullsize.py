@@ -1,0 +1,191 @@
+"""Full-frame parity at the configurations' full sizes (GPU only).
+
+Every pixel of every image is compared with the oracle (hit cell, layer, face
+and shadow bit exact; depth within 1e-5 relative; colour within 1/255), in the
+launch configuration the benchmark times and in the library's default one:
+
+* the eye-level 1920 x 1080 view over the 2048 x 2048 world with walls and
+  caves, with shadow rays;
+* all 64 cameras of the batched-cameras workload (16 x 3840 x 2160,
+  24 x 1920 x 1080, 24 x 640 x 360, 188,006,400 primary rays plus shadow
+  rays), one batched launch, tuned (4 x 32 tiles, mip start 5), default and
+  plain (one launch per camera), the three bit-identical;
+* every 100th frame of the 1000-frame fly-through over the 2048 x 16384
+  world, tuned (4 x 32, mip start 9) and default;
+* the serving loop on the 2048 x 16384 world at the serving resolutions
+  (640 x 360 to 3840 x 2160) with crater edits every 11th request: each served
+  image equals the same request rendered alone on a fresh world holding
+  exactly the edits before it, bit for bit, and the oracle on that world
+  (every pixel up to 1920 x 1080, 40,000 sampled pixels per 3840 x 2160 image).
+
+The paper evaluates its renderers against a CPU ray cast (Section 4.1); here
+the CPU ray cast is the oracle and the bar is exact.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from hfcheck import compare, sample_pixels
+
+pytestmark = pytest.mark.gpu
+NT = os.cpu_count() or 4
+
+
+@pytest.fixture(scope="module")
+def hf():
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+    import paper_2608_17390_gb300 as m
+
+    return m
+
+
+def _host(out, pix=None):
+    """One camera's device outputs as numpy arrays (optionally at pix)."""
+    import torch
+
+    d = {}
+    idx = None if pix is None else torch.from_numpy(np.asarray(pix, np.int64)).cuda()
+    for k, t in out.items():
+        a = (t if idx is None else t[idx]).cpu().numpy()
+        if k in ("hit_cell", "rgba"):
+            a = a.view(np.uint32)
+        d[k] = a
+    return d
+
+
+def _render(hf, ctx, cams, shadows, opts):
+    import torch
+
+    outs = hf.alloc_outputs(cams, device="cuda", shadows=shadows)
+    hf.hf_render(ctx, cams, outs, opts)
+    hf.hf_sync(ctx)
+    torch.cuda.synchronize()
+    return outs
+
+
+def _assert_identical(a, b, what):
+    import torch
+
+    for k in a:
+        assert torch.equal(a[k], b[k]), "%s: %s differs" % (what, k)
+
+
+def test_c2_full_frame_at_1080p(hf):
+    cfg = synth.config_c2()
+    cells, cams = cfg["cells"], cfg["cams"]
+    ctx = hf.hf_create(cells)
+    try:
+        g = _render(hf, ctx, cams, True, hf.make_opts(flags=hf.HF_SHADOWS))
+        b = _render(hf, ctx, cams, True, hf.make_opts(flags=hf.HF_SHADOWS | hf.HF_NOGRAPH,
+                                                      tile_w=4, tile_h=32))
+        _assert_identical(g[0], b[0], "C2 default vs 4x32")
+        o = oracle.render(cells, cams[0], shadows=True, nthreads=NT)
+        compare(_host(g[0]), o, shadows=True, what="C2 1920x1080")
+        assert (o["face"] != 255).mean() > 0.3 and 0 < o["shadow"].sum()
+    finally:
+        hf.hf_destroy(ctx)
+
+
+def test_c3_every_camera_full_frame(hf):
+    """The benchmark's batched workload, every pixel of every camera."""
+    cfg = synth.config_c3()
+    cells, cams = cfg["cells"], cfg["cams"]
+    assert sum(int(c["w"]) * int(c["h"]) for c in cams) == 188006400
+    ctx = hf.hf_create(cells)
+    try:
+        tuned = _render(hf, ctx, cams, True,
+                        hf.make_opts(tile_w=4, tile_h=32, mip_start=5, flags=hf.HF_SHADOWS))
+        default = _render(hf, ctx, cams, True, hf.make_opts(flags=hf.HF_SHADOWS))
+        plain = _render(hf, ctx, cams, True, hf.make_opts(flags=hf.HF_SHADOWS | hf.HF_PLAIN))
+        for i in range(len(cams)):
+            _assert_identical(tuned[i], default[i], "C3 cam %d tuned vs default" % i)
+            _assert_identical(tuned[i], plain[i], "C3 cam %d batched vs plain" % i)
+        del default, plain
+        hits = 0
+        for i, c in enumerate(cams):
+            o = oracle.render(cells, c, shadows=True, nthreads=NT)
+            compare(_host(tuned[i]), o, shadows=True, what="C3 cam %d (%dx%d)" % (
+                i, int(c["w"]), int(c["h"])))
+            hits += int((o["face"] != 255).sum())
+        assert hits > 0.5 * 188006400
+    finally:
+        hf.hf_destroy(ctx)
+
+
+def test_c4_every_100th_frame_full(hf):
+    cells = synth.config_c4()["cells"]
+    frames = synth.config_c4_frames(cells, 1000)[::100]
+    ctx = hf.hf_create(cells)
+    try:
+        tuned = _render(hf, ctx, frames, False, hf.make_opts(tile_w=4, tile_h=32, mip_start=9))
+        default = _render(hf, ctx, frames, False, hf.make_opts())
+        for i in range(len(frames)):
+            _assert_identical(tuned[i], default[i], "C4 frame %d tuned vs default" % (100 * i))
+        del default
+        for i, c in enumerate(frames):
+            o = oracle.render(cells, c, nthreads=NT)
+            compare(_host(tuned[i]), o, what="C4 frame %d" % (100 * i))
+    finally:
+        hf.hf_destroy(ctx)
+
+
+def test_c5_serving_on_the_large_world(hf):
+    """The native serving loop on the 2048 x 16384 world at the serving
+    resolutions, edits interleaved 10 renders : 1 crater, several batches in
+    flight on separate lanes."""
+    import torch
+
+    cells = synth.config_c4()["cells"]
+    records = synth.poisson_requests(cells, 44, rate=4000.0, seed=21, edit_every=11)
+    renders = [i for i, r in enumerate(records) if r["kind"] == "render"]
+    assert len(renders) == 40 and {(int(records[i]["cam"]["w"]), int(records[i]["cam"]["h"]))
+                                   for i in renders} == set(synth.SERVING_RESOLUTIONS)
+    outs = [None if r["kind"] == "edit" else hf.alloc_outputs(np.array([r["cam"]]))[0]
+            for r in records]
+    ctx = hf.hf_create(cells)
+    try:
+        res = hf.hf_serve_replay(ctx, records, lanes=8, max_batch=8, output_budget=4 << 30,
+                                 outputs=outs)
+        hf.hf_sync(ctx)
+        torch.cuda.synchronize()
+    finally:
+        hf.hf_destroy(ctx)
+    assert len(set(res["batch"][res["batch"] != 0xFFFFFFFF])) > 3
+    world = cells.copy()
+    checked = 0
+    k = 0
+    while k < len(records):
+        j = k
+        while j < len(records) and records[j]["kind"] == "render":
+            j += 1
+        if j > k:  # renders k..j-1 were admitted after the same edits
+            fresh = hf.hf_create(world)
+            try:
+                for i in range(k, j):
+                    cam = np.array([records[i]["cam"]])
+                    assert int(res["version"][i]) == sum(
+                        r["kind"] == "edit" for r in records[:i])
+                    alone = _render(hf, fresh, cam, False, hf.make_opts())
+                    _assert_identical(outs[i], alone[0], "served request %d vs alone" % i)
+                    w, h = int(cam[0]["w"]), int(cam[0]["h"])
+                    pix = None if w * h <= 1920 * 1080 else sample_pixels(w, h, 40000, i)
+                    o = oracle.render(world, cam[0], pix=pix, nthreads=NT)
+                    compare(_host(outs[i], pix), o, what="served request %d (%dx%d)" % (i, w, h))
+                    checked += 1
+            finally:
+                hf.hf_destroy(fresh)
+        if j < len(records):  # the edit at j
+            x0, y0, blk = records[j]["edit"]
+            world[y0:y0 + blk.shape[0], x0:x0 + blk.shape[1]] = blk
+        k = j + 1
+    assert checked == 40

@@ -101,6 +101,8 @@ def test_native_loop_orders_edits_and_leaves_the_edited_world(hf):
             if rec["kind"] == "edit":
                 edits_before += 1
                 assert r.version == edits_before
+                # done is the device completion of the edit, on the host clock
+                assert r.admitted >= r.arrival - 1e-4 and r.done >= r.admitted - 1e-4
                 x0, y0, blk = rec["edit"]
                 world[y0:y0 + blk.shape[0], x0:x0 + blk.shape[1]] = blk
             else:

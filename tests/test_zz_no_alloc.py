@@ -85,8 +85,65 @@ def test_noalloc_rejects_oversize_batches_and_foreign_streams(hf):
         with pytest.raises(hf.HFError) as e:
             hf.hf_render_noalloc(ctx, cam, outs[:1], hf.make_opts(stream=s.cuda_stream))
         assert e.value.code == hf.HF_E_INVALID_ARG
+        # flags it cannot honour are refused, not dropped
+        for flag in (hf.HF_STATS, hf.HF_PLAIN, hf.HF_NOGRAPH, hf.HF_NOWAIT, hf.HF_HOST_OUTPUTS,
+                     hf.HF_HOST_STAGED):
+            with pytest.raises(hf.HFError) as e:
+                hf.hf_render_noalloc(ctx, cam, outs[:1], hf.make_opts(flags=hf.HF_SYNC | flag))
+            assert e.value.code == hf.HF_E_INVALID_ARG, flag
         # the largest allowed batch still renders
         hf.hf_render_noalloc(ctx, many[:-1], outs[:-1], hf.make_opts(flags=hf.HF_SYNC))
         hf.hf_sync(ctx)
+    finally:
+        hf.hf_destroy(ctx)
+
+
+def test_noalloc_allocates_nothing_after_its_first_call(hf):
+    """The defining property: once the first call on a device has looked up
+    the scratch array's address, further calls (of several batch sizes) leave
+    the device's free memory unchanged."""
+    import torch
+
+    cfg = synth.config_c3(scale=16)
+    cells, cams = cfg["cells"], cfg["cams"]
+    ctx = hf.hf_create(cells)
+    try:
+        batches = [cams[:40], cams[5:6], cams[10:33], cams[:64]]
+        outs = [hf.alloc_outputs(b, device="cuda", shadows=True) for b in batches]
+        opts = hf.make_opts(flags=hf.HF_SHADOWS | hf.HF_SYNC)
+        hf.hf_render_noalloc(ctx, batches[0], outs[0], opts)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        for _ in range(3):
+            for b, o in zip(batches, outs):
+                hf.hf_render_noalloc(ctx, b, o, opts)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+    finally:
+        hf.hf_destroy(ctx)
+
+
+def test_noalloc_reports_the_step_guard_and_recovers(hf):
+    """With HF_SYNC, a step guard of one iteration makes rays stop early: the
+    call returns HF_E_STEP_LIMIT, the stopped pixels carry the error face, and
+    the next call (default guard) renders normally, equal to hf_render."""
+    cfg = synth.config_c1()
+    cells, cams = cfg["cells"], cfg["cams"]
+    ctx = hf.hf_create(cells)
+    try:
+        import torch
+
+        outs = hf.alloc_outputs(cams, device="cuda", shadows=True)
+        with pytest.raises(hf.HFError) as e:
+            hf.hf_render_noalloc(ctx, cams, outs,
+                                 hf.make_opts(flags=hf.HF_SHADOWS | hf.HF_SYNC, max_steps=1))
+        assert e.value.code == hf.HF_E_STEP_LIMIT
+        torch.cuda.synchronize()
+        assert (outs[0]["face"] == 254).any()
+        got = _noalloc(hf, ctx, cams, hf.make_opts(flags=hf.HF_SHADOWS | hf.HF_SYNC))
+        ref = gpu_render(hf, ctx, cams, shadows=True, opts=hf.make_opts(flags=hf.HF_SHADOWS))
+        ref0 = {k: v.astype(np.float64) if k == "depth" else v for k, v in ref[0].items()}
+        compare(got[0], ref0, shadows=True, what="noalloc after the step guard")
+        assert (got[0]["face"] != 254).all()
     finally:
         hf.hf_destroy(ctx)
