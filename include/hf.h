@@ -207,7 +207,13 @@ int hf_create_pairs(const hf_pair_desc *desc, hf_ctx **out);
 int hf_edit(hf_ctx *ctx, uint32_t x0, uint32_t y0, uint32_t w, uint32_t h,
             const uint32_t *cells, size_t row_stride);
 
-/* Render n cameras (HOST array) into outs[0..n-1] (HOST array of structs that
+/* Render n cameras (HOST array) into outs[0..n-1]: per pixel, the first solid
+ * point of its ray under the SOLID predicate of Section 3.1 (closed ends, the
+ * floor unbounded below), the exact result of the flat per-cell CPU ray cast
+ * the paper evaluates its renderers against (Section 4.1); misses keep the
+ * cleared far values rather than a made-up ground hit (Section 3.1).  The hit
+ * record layout is given at hf_outputs; shading and the optional shadow ray
+ * at hf_render_opts.  outs is a HOST array of structs that
  * hold DEVICE pointers, or pinned HOST pointers with HF_HOST_OUTPUTS: each
  * non-NULL one is then checked with cudaPointerGetAttributes and replaced by
  * its device alias; the results are in host memory once the render's stream
@@ -379,8 +385,10 @@ int hf_render_march(hf_ctx *ctx, const hf_camera *cams, uint32_t n, const hf_out
  * hf_sync hit its step guard (and clears that flag), else HF_OK / HF_E_CUDA. */
 int hf_sync(hf_ctx *ctx);
 
-/* Synchronise, then free every device and host resource of the context.
- * NULL is accepted.  Returns HF_OK or HF_E_CUDA. */
+/* The end of a context's life (the paper has no counterpart: its renderers
+ * release their GPU resources with the graphics device).  Synchronise, then
+ * free every device and host resource of the context.  NULL is accepted.
+ * Returns HF_OK or HF_E_CUDA. */
 int hf_destroy(hf_ctx *ctx);
 
 /* Host helper: quantise a pose into an integer camera, in float64.  yaw 0
@@ -409,7 +417,9 @@ int hf_validate_cells(const uint32_t *cells, size_t n, size_t *bad_index);
 int hf_validate_pairs(const uint16_t *texels, uint32_t width, uint32_t height, size_t row_stride,
                       size_t *bad_index);
 
-/* Static text for a code (never NULL). */
+/* Static text for one of the HF_E_* codes above (a library convention: the
+ * paper defines no error reporting).  Never NULL; an unknown code gives
+ * "unknown error". */
 const char *hf_strerror(int code);
 
 /* Sizes and device of a context.  Errors: HF_E_INVALID_ARG. */

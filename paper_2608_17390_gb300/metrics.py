@@ -7,9 +7,10 @@ a reference rendering of the same cameras.
   renderer fills;
 * geometry: median and 95th percentile of |depth difference| over pixels
   where both have terrain;
-* coherence: the fraction of pixels whose distance disagrees with their own
-  3 x 3 neighbourhood, minus the same fraction for the reference (clamped at
-  zero).  The paper does not fix "disagrees"; here a pixel disagrees when its
+* coherence: how many pixels (as a share of the image) have a depth at odds
+  with the pixels around them in their 3 x 3 block, beyond the reference's
+  own share of such pixels (never below zero).  The paper leaves "at odds"
+  open; here a pixel is at odds when its
   terrain/background status differs from the majority of its 8 neighbours,
   or, for a terrain pixel among terrain neighbours, when its depth differs
   from the neighbourhood median by more than `rel_tol` of that median.

@@ -4,9 +4,10 @@
   hits, and its depth lies in the bracket the four bisections leave:
   [t*, t* + dt/16] times |d| (dt = the sample spacing).
 * A one-cell wall is skipped by most horizontal rays when the sample spacing
-  (600 / 129 = 4.65 cells) exceeds its width -- the method's trade-off the
-  paper states ("a sample interval can still skip a thinner feature") -- and
-  found by every ray once the spacing is below one cell.
+  (600 / 129 = 4.65 cells) exceeds its width -- the trade-off the paper
+  acknowledges for its march: a feature narrower than the step can fall
+  between two samples -- and found by every ray once the spacing is below
+  one cell.
 * Misses stay misses: no hit is made at the ground plane or outside the grid.
 * A ray whose samples and bisection midpoints are exact in float32 pins the
   spacing t_end / (steps + 1), the clip at z = 0, the number of bisections
