@@ -159,7 +159,14 @@ typedef struct {
                                 | HF_HOST_OUTPUTS | HF_HOST_STAGED */
     uint32_t max_steps;      /* traversal iterations allowed per ray; 0 = default guard */
     int32_t sun[3];          /* direction toward the sun; all zero = (321060, -321060, 262144),
-                                elevation 30 deg, azimuth 135 deg; each |sun_i| < 2^21 */
+                                elevation 30 deg, azimuth 135 deg; each |sun_i| < 2^21.
+                                With HF_SHADOWS and a sun that rises (sun[2] > 0), is not
+                                vertical, and clears the 255-unit height range within
+                                1024 cells, the first such render builds per-cell shadow
+                                bounds for this sun (4 bytes per cell, allocated then,
+                                rebuilt when a render asks for another sun, repaired by
+                                hf_edit): a shadow ray whose origin they decide is not
+                                traced; the shadow bit is the same either way. */
     void *cuda_stream;       /* stream for this render; NULL = the context's stream */
 } hf_render_opts;
 
@@ -441,9 +448,21 @@ int hf_read_pyramid(hf_ctx *ctx, uint32_t level, uint32_t *out);
  * runs).  Errors: HF_E_INVALID_ARG, HF_E_CUDA. */
 int hf_rebuild(hf_ctx *ctx);
 
+/* Copy the per-cell shadow bounds last built by a render with HF_SHADOWS to
+ * HOST memory (synchronous): W*H words, row-major, word = F | G << 16 with F
+ * and G in units of 2^-8 world units: a shadow ray toward sun[] starting in
+ * the cell (the cell it occupies just after t = 0) at height <= F*256 (in
+ * 2^-16 units) is occluded, at height >= G*256 lit.  out may be NULL (only
+ * sun[] is written); sun may be NULL.  The paper has no counterpart: its
+ * shadow-map pass (Section 3) precomputes sun visibility approximately; these
+ * bounds are exact but partial.
+ * Errors: HF_E_INVALID_ARG (null ctx, or no bounds built), HF_E_CUDA. */
+int hf_read_sun_bounds(hf_ctx *ctx, uint32_t *out, int32_t sun[3]);
+
 /* Synchronise and read the fetch counters accumulated by HF_STATS renders:
  * out[0] pyramid node fetches, out[1] cell fetches, out[2] primary rays,
- * out[3] shadow rays, out[4] fetches made by shadow rays.  Clears them.
+ * out[3] shadow rays, out[4] fetches made by shadow rays (a shadow-bound
+ * lookup counts as one).  Clears them.
  * Errors: HF_E_INVALID_ARG, HF_E_CUDA. */
 int hf_stats(hf_ctx *ctx, uint64_t out[5]);
 

@@ -4,7 +4,7 @@ A thin ctypes layer over the C ABI in include/hf.h, with the same names:
 ``hf_create``, ``hf_edit``, ``hf_render``, ``hf_render_noalloc``, ``hf_render_march``,
 ``hf_sync``, ``hf_destroy``,
 ``hf_camera_from_pose``, ``hf_validate_camera``, ``hf_validate_cells``,
-``hf_strerror``, ``hf_info``, ``hf_read_cells``, ``hf_read_pyramid``,
+``hf_strerror``, ``hf_info``, ``hf_read_cells``, ``hf_read_pyramid``, ``hf_read_sun_bounds``,
 ``hf_rebuild``, ``hf_stats``.  It only marshals arguments: every step of the
 ray cast runs in the library's CUDA kernels.  PyTorch provides device memory
 (output tensors) and streams.
@@ -182,6 +182,7 @@ _SIGS = {
     "hf_info": ([_P, ctypes.POINTER(hf_info_t)], ctypes.c_int),
     "hf_read_cells": ([_P, _U32, _U32, _U32, _U32, _P, ctypes.c_size_t], ctypes.c_int),
     "hf_read_pyramid": ([_P, _U32, _P], ctypes.c_int),
+    "hf_read_sun_bounds": ([_P, _P, _P], ctypes.c_int),
     "hf_rebuild": ([_P], ctypes.c_int),
     "hf_stats": ([_P, _P], ctypes.c_int),
     "hf_serve_replay": ([_P, _P, _U32, ctypes.POINTER(hf_serve_opts), _P], ctypes.c_int),
@@ -468,6 +469,16 @@ def hf_read_pyramid(ctx, level):
     out = np.empty((hk, wk), np.uint32)
     _check(lib.hf_read_pyramid(ctx, level, out.ctypes.data), "hf_read_pyramid")
     return out
+
+
+def hf_read_sun_bounds(ctx):
+    """The per-cell shadow bounds last built by a shadowed render:
+    (uint32 [H, W] of F | G << 16 in 2^-8 world units, (sun x, y, z))."""
+    info = hf_info(ctx)
+    out = np.empty((info["height"], info["width"]), np.uint32)
+    sun = (ctypes.c_int32 * 3)()
+    _check(lib.hf_read_sun_bounds(ctx, out.ctypes.data, sun), "hf_read_sun_bounds")
+    return out, tuple(sun)
 
 
 def hf_rebuild(ctx):

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhf.so")
 SOURCES = ["hf_api.cpp", "hf_trace.cu", "hf_pyramid.cu", "hf_march.cu", "hf_scatter.cu", "hf_voxel.cu",
-           "hf_serve.cpp"]
+           "hf_serve.cpp", "hf_sun.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -68,6 +68,9 @@ struct hf_ctx {
     int occ[2][2] = {{0, 0}, {0, 0}};
     int occ_march = 0;
     bool pair = false;  // level 0 holds paired 2-byte texels (hf_create_pairs)
+    uint32_t *d_sun = nullptr;  // per-cell shadow bounds (hf_sun.cu), allocated on first use
+    bool sun_valid = false;     // d_sun holds the bounds of sun_dir for the current cells
+    int32_t sun_dir[3] = {0, 0, 0};
     uint32_t *d_vox = nullptr;  // voxel occupancy pyramid (hf_voxel_build), or null
     size_t vox_words = 0;
     hf::VoxelDev vd{};
@@ -313,6 +316,7 @@ int hf_destroy(hf_ctx *c) {
     if (c->d_stats) cudaFree(c->d_stats);
     if (c->d_world) cudaFree(c->d_world);
     if (c->d_vox) cudaFree(c->d_vox);
+    if (c->d_sun) cudaFree(c->d_sun);
     if (c->render2) {
         if (cudaStreamSynchronize(c->render2) != cudaSuccess) rc = HF_E_CUDA;
         cudaStreamDestroy(c->render2);
@@ -521,6 +525,13 @@ int hf_edit(hf_ctx *c, uint32_t x0, uint32_t y0, uint32_t w, uint32_t h, const u
     if (c->d_vox && hf::voxel_repair(c->wd, c->vd, (int32_t)x0, (int32_t)y0, (int32_t)(x0 + w),
                                      (int32_t)(y0 + h), false, c->stream))
         return HF_E_CUDA;
+    if (c->sun_valid) {  // the shadow bounds of the cells upstream of the rectangle
+        if (hf::sun_bounds_repair(c->wd, c->d_sun, c->sun_dir, (int32_t)x0, (int32_t)y0,
+                                  (int32_t)(x0 + w), (int32_t)(y0 + h), c->stream)) {
+            c->sun_valid = false;
+            return HF_E_CUDA;
+        }
+    }
     CK(cudaEventRecord(c->edit_done, c->stream));
     return HF_OK;
 }
@@ -535,6 +546,11 @@ int hf_rebuild(hf_ctx *c) {
         CK(cudaMemsetAsync(c->d_vox, 0, c->vox_words * 4, c->stream));
         if (hf::voxel_repair(c->wd, c->vd, 0, 0, (int32_t)c->W, (int32_t)c->H, true, c->stream))
             return HF_E_CUDA;
+    }
+    if (c->sun_valid &&
+        hf::sun_bounds(c->wd, c->d_sun, c->sun_dir, 0, 0, (int32_t)c->W, (int32_t)c->H, c->stream)) {
+        c->sun_valid = false;
+        return HF_E_CUDA;
     }
     CK(cudaEventRecord(c->edit_done, c->stream));
     return HF_OK;
@@ -593,6 +609,18 @@ int hf_read_pyramid(hf_ctx *c, uint32_t level, uint32_t *out) {
     return HF_OK;
 }
 
+int hf_read_sun_bounds(hf_ctx *c, uint32_t *out, int32_t sun[3]) {
+    if (!c) return HF_E_INVALID_ARG;
+    if (!c->sun_valid) return HF_E_INVALID_ARG;
+    if (sun)
+        for (int i = 0; i < 3; ++i) sun[i] = c->sun_dir[i];
+    if (!out) return HF_OK;
+    CK(cudaSetDevice(c->device));
+    CK(cudaMemcpyAsync(out, c->d_sun, (size_t)c->W * c->H * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return HF_OK;
+}
+
 int hf_stats(hf_ctx *c, uint64_t out[5]) {
     if (!c || !out) return HF_E_INVALID_ARG;
     CK(cudaSetDevice(c->device));
@@ -603,6 +631,38 @@ int hf_stats(hf_ctx *c, uint64_t out[5]) {
     CK(cudaMemsetAsync(c->d_stats, 0, sizeof(v), c->stream));
     CK(cudaStreamSynchronize(c->stream));
     for (int i = 0; i < 5; ++i) out[i] = v[i];
+    return HF_OK;
+}
+
+// The shadow bounds of `sun` for the current cells, built on the context's
+// stream when the sun differs from the last one (or after a failure); renders
+// issued later wait for it like for an edit.  Suns without bounds (not
+// rising, vertical, or too low: hf::sun_bounds_eligible) give null.
+static int ensure_sun_bounds(hf_ctx *c, const int32_t sun[3], const uint32_t **out) {
+    *out = nullptr;
+    if (!hf::sun_bounds_eligible(sun)) return HF_OK;
+    if (c->sun_valid && std::memcmp(c->sun_dir, sun, sizeof(c->sun_dir)) == 0) {
+        *out = c->d_sun;
+        return HF_OK;
+    }
+    CK(cudaSetDevice(c->device));
+    if (!c->d_sun) {
+        if (cudaMalloc(&c->d_sun, (size_t)c->W * c->H * sizeof(uint32_t)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            c->d_sun = nullptr;
+            return HF_E_OOM;
+        }
+    }
+    // no render in flight may read bounds of another sun while they change
+    for (auto &s : c->slots)
+        if (s.pending) CK(cudaStreamWaitEvent(c->stream, s.done, 0));
+    c->sun_valid = false;
+    if (hf::sun_bounds(c->wd, c->d_sun, sun, 0, 0, (int32_t)c->W, (int32_t)c->H, c->stream))
+        return HF_E_CUDA;
+    CK(cudaEventRecord(c->edit_done, c->stream));
+    std::memcpy(c->sun_dir, sun, sizeof(c->sun_dir));
+    c->sun_valid = true;
+    *out = c->d_sun;
     return HF_OK;
 }
 
@@ -1023,10 +1083,18 @@ int hf_render(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_outputs *ou
     const uint64_t guard = 4ull * (c->W + c->H) + 64;
     const uint32_t steps = o.max_steps ? o.max_steps : (uint32_t)(guard > 0x7FFFFFFF ? 0x7FFFFFFF : guard);
     if (steps > 0x7FFFFFFFu) return HF_E_INVALID_ARG;
+    for (uint32_t i = 0; i < n; ++i)  // before anything is built or enqueued
+        if (hf_validate_camera(c->W, c->H, &cams[i]) != HF_OK) return HF_E_INVALID_ARG;
+    const uint32_t *bounds = nullptr;
+    if (shadows) {
+        const int brc = ensure_sun_bounds(c, sun, &bounds);
+        if (brc != HF_OK) return brc;
+    }
     Batch b;
     int rc = prepare_batch(c, cams, n, outs, tw, th, (o.flags & HF_NOWAIT) != 0, o.cuda_stream, b,
                            (o.flags & HF_HOST_OUTPUTS) != 0);
     if (rc != HF_OK) return rc;
+    b.p.sun_bounds = bounds;
     Slot &s = c->slots[b.slot];
     hf::RenderParams &p = b.p;
     p.mip_start = (int32_t)mip_c;

@@ -132,6 +132,7 @@ struct RenderParams {
     int32_t max_steps;
     int32_t sun[3];
     float sun_n[3];                // sun / |sun|
+    const uint32_t *sun_bounds;    // per-cell shadow bounds for `sun` (hf_sun.cu), or null
 };
 
 // Parameters of the fixed-step comparison marcher (hf_march.cu).
@@ -198,6 +199,24 @@ struct CtxView {
     int occ_shadows[2];  // batched-kernel blocks per SM without / with shadow rays
 };
 int ctx_view(const ::hf_ctx *ctx, CtxView *out);
+
+// Shadow bounds (hf_sun.cu): per cell, F | G << 16 in 2^-8 world units: a
+// shadow ray toward `sun` starting in the cell at height <= F << 8 is
+// occluded, at >= G << 8 lit.  Only for rising, non-vertical suns whose rays
+// clear the 255-unit height range within kSunMaxReach cells.
+constexpr int64_t kSunMaxReach = 1024;
+bool sun_bounds_eligible(const int32_t sun[3]);
+// Recompute the bounds of the cells of [x0, x1) x [y0, y1) from the cells.
+int sun_bounds(const WorldDev &w, uint32_t *bounds, const int32_t sun[3], int32_t x0, int32_t y0,
+               int32_t x1, int32_t y1, void *stream);
+// Recompute, after an edit of the cells of [x0, x1) x [y0, y1), the bounds
+// that depend on them (the pyramid must already be repaired).
+int sun_bounds_repair(const WorldDev &w, uint32_t *bounds, const int32_t sun[3], int32_t x0,
+                      int32_t y0, int32_t x1, int32_t y1, void *stream);
+// The cells whose bounds depend on the cells of [x0, x1) x [y0, y1) lie in
+// out = {x0', y0', x1', y1'} (clipped to the grid).
+void sun_bounds_region(const WorldDev &w, const int32_t sun[3], int32_t x0, int32_t y0,
+                       int32_t x1, int32_t y1, int32_t *out);
 
 // Pyramid (hf_pyramid.cu): repair the nodes covering cell rectangle
 // [x0, x1) x [y0, y1) at every level 1..L, in order.

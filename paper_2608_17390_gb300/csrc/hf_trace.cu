@@ -446,13 +446,29 @@ __device__ __forceinline__ void trace_pixel(const RenderParams &p, const LevelDe
             case kFaceNZ: szp -= 1; break;
             default: szp += 1; break;
         }
+        if (STATS) nshadow++;
+        if (p.sun_bounds) {
+            // the start cell's proven bounds decide most shadow rays at once:
+            // at or below F occluded, at or above G lit (hf_sun.cu)
+            int32_t bx = sxp >> kShift, by = syp >> kShift;
+            if (p.sun[0] < 0 && (sxp & 0xFFFF) == 0) bx -= 1;
+            if (p.sun[1] < 0 && (syp & 0xFFFF) == 0) by -= 1;
+            if ((uint32_t)bx < (uint32_t)p.world.W && (uint32_t)by < (uint32_t)p.world.H) {
+                const uint32_t fg = __ldg(p.sun_bounds + (uint32_t)by * (uint32_t)p.world.W + (uint32_t)bx);
+                if (STATS) scnt.cells++;
+                if (szp <= (int32_t)((fg & 0xFFFFu) << 8)) {
+                    visible = false;
+                    break;
+                }
+                if (szp >= (int32_t)((fg >> 16) << 8)) break;
+            }
+        }
         r.ox = sxp;
         r.oy = syp;
         r.oz = szp;
         r.dx = p.sun[0];
         r.dy = p.sun[1];
         r.dz = p.sun[2];
-        if (STATS) nshadow++;
         shadow_pass = true;
     }
     store_pixel(p, c, (uint32_t)py * c.w + (uint32_t)px, ph, depth, visible, SHADOWS);
