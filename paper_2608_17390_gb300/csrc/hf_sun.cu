@@ -73,111 +73,124 @@ __device__ __forceinline__ uint32_t word_at(const WorldDev &w, const SunAxes &a,
     return a.x_major ? cell_node(w, cu, cv) : cell_node(w, cv, cu);
 }
 
-// Level-4 node (16 x 16 cells) at major / minor node coordinates.
-__device__ __forceinline__ uint32_t node4_at(const WorldDev &w, const SunAxes &a, int32_t nu,
+// floor(a / b) for b > 0 and |a / b| < 2^22: a float estimate, then one
+// exact correction (the estimate's relative error is a few 2^-24, so it is
+// off by at most one).  Integer division by a run-time 64-bit divisor is a
+// long software routine on the GPU; this is a handful of instructions.
+__device__ __forceinline__ int64_t floor_div_est(int64_t a, int64_t b, float rcp_b) {
+    int64_t q = (int64_t)floorf((float)a * rcp_b);
+    const int64_t r = a - q * b;
+    if (r < 0) q -= 1;
+    else if (r >= b) q += 1;
+    return q;
+}
+
+// Level-5 node (32 x 32 cells) at major / minor node coordinates.
+__device__ __forceinline__ uint32_t node5_at(const WorldDev &w, const SunAxes &a, int32_t nu,
                                              int32_t nv) {
     const int32_t x = a.x_major ? nu : nv, y = a.x_major ? nv : nu;
-    return __ldg(w.base + w.off[4] + (uint32_t)y * w.stride[4] + (uint32_t)x);
+    return __ldg(w.base + w.off[5] + (uint32_t)y * w.stride[5] + (uint32_t)x);
 }
 
-constexpr int32_t kBlock = 16;  // columns per pyramid-level-4 skip test
-
-// Largest max-floor (byte 0) and max-top (byte 2) over the level-4 nodes
-// covering columns cu + smaj*[k, k + kBlock) and the rows every band of those
-// columns spans (clipped to the grid).  Returns false when that region lies
-// wholly outside the grid along the minor axis.
-__device__ bool block_max(const WorldDev &w, const SunAxes &a, int32_t cu, int32_t cv, int32_t k,
-                          int32_t NU, int32_t NV, int64_t &maxh0, int64_t &maxtop) {
-    const int64_t lmaj = a.lmaj, lmin = a.lmin;
-    const int64_t lo = min(lmin * (k - 1), lmin * (k + kBlock)),
-                  hi = max(lmin * (k - 1), lmin * (k + kBlock));
-    int32_t r0 = cv + (int32_t)floor_div64(lo, lmaj), r1 = cv + 1 + (int32_t)floor_div64(hi, lmaj);
-    if (r1 < 0 || r0 >= NV) return false;
-    r0 = max(r0, 0);
-    r1 = min(r1, NV - 1);
-    int32_t c0 = cu + a.smaj * k, c1 = cu + a.smaj * (k + kBlock - 1);
-    if (c0 > c1) {
-        const int32_t t = c0;
-        c0 = c1;
-        c1 = t;
-    }
-    c0 = max(c0, 0);
-    c1 = min(c1, NU - 1);
-    maxh0 = 0;
-    maxtop = 0;
-    for (int32_t nu = c0 >> 4; nu <= c1 >> 4; ++nu)
-        for (int32_t nv = r0 >> 4; nv <= r1 >> 4; ++nv) {
-            const uint32_t n = node4_at(w, a, nu, nv);
-            maxh0 = max(maxh0, (int64_t)(n & 0xFF));
-            maxtop = max(maxtop, (int64_t)((n >> 16) & 0xFF));
-        }
-    return true;
-}
-
-// F and G of the cell at major / minor coordinates (cu, cv), scaled by lmaj
-// (heights in 2^-16 world units times lmaj).  Where the pyramid has a level 4,
-// blocks of kBlock columns whose highest floor (for F) or top (for G) cannot
-// raise the bound are skipped whole; the result is the same value.
-__device__ void bounds_of(const WorldDev &w, const SunAxes &a, int32_t cu, int32_t cv, int32_t NU,
-                          int32_t NV, int64_t &F, int64_t &G) {
+// F and G of the cell at major / minor coordinates (cu, cv), rounded to the
+// stored units (F down, G up, 2^-8 world units), computed by the 32 lanes of a
+// warp: lane l takes column k = k0 + l of each round of 32 (its band's lowest
+// floor for F, its widest band's highest top for G), and the warp keeps the
+// largest term.  Rounding is monotone, so the largest rounded term is the
+// rounded largest term: lanes round first and reduce in 32 bits.  A bound
+// stops at the first column it cannot use any more (the grid's end, or for F
+// a band that leaves the grid -- monotone in k, so every lane past it is out
+// too) or once no later column can raise it.  Where the pyramid has a level
+// 5, a round whose region's highest floor (F) or top (G) cannot raise the
+// bound loads no cells; the result is the same.
+__device__ void bounds_of_warp(const WorldDev &w, const SunAxes &a, int32_t cu, int32_t cv,
+                               int32_t NU, int32_t NV, int lane, int32_t &F16, int32_t &G16) {
+    const unsigned full = 0xFFFFFFFFu;
     const int64_t lmaj = a.lmaj, lmin = a.lmin, lz = a.lz;
-    const int64_t top_all = 255 * kS * lmaj;
-    const bool skip = w.L >= 4;
-    // F: k = 0 is the start cell's floor
-    F = (int64_t)(word_at(w, a, cu, cv) & 0xFF) * kS * lmaj;
-    for (int32_t k = 1;;) {
+    const int64_t unit = lmaj << 8;
+    const float rcp_maj = 1.0f / (float)lmaj, rcp_unit = 1.0f / (float)unit;
+    const int64_t top_all = 255 * kS * lmaj, rise1 = kS * lz;
+    // rounded terms: negative ones never win (F, G >= 0 from k = 0)
+    auto q_floor = [&](int64_t v) -> int32_t {
+        return v < 0 ? -1 : (int32_t)min(floor_div_est(v, unit, rcp_unit), (int64_t)65535);
+    };
+    auto q_ceil = [&](int64_t v) -> int32_t {
+        return v <= 0 ? 0 : (int32_t)min(-floor_div_est(-v, unit, rcp_unit), (int64_t)65535);
+    };
+    const uint32_t c0 = word_at(w, a, cu, cv);
+    F16 = q_floor((int64_t)(c0 & 0xFF) * kS * lmaj);  // k = 0: the start cell's floor
+    {  // G, k = 0: the rows the ray can cross in its start column (it moves at
+       // most one row there, |lmin| <= lmaj), strictly above
+        const int32_t r0 = cv + (lmin < 0 ? -1 : 0), r1 = cv + 1;
+        int32_t t = -1;
+        if (lane <= r1 - r0) {
+            const int32_t r = r0 + lane;
+            if (r >= 0 && r < NV) t = (int32_t)((word_at(w, a, cu, r) >> 16) & 0xFF);
+        }
+        t = __reduce_max_sync(full, t);
+        G16 = q_ceil(((int64_t)t * kS + 1) * lmaj);
+    }
+    const bool skip = w.L >= 5;
+    bool f_on = true, g_on = true;
+    for (int32_t k0 = 1;; k0 += 32) {
+        // no column from k0 on can raise a bound already this high
+        if (f_on && top_all - (int64_t)k0 * rise1 < (int64_t)(F16 + 1) * unit) f_on = false;
+        if (g_on && top_all - (int64_t)(k0 - 1) * rise1 <= (int64_t)G16 * unit) g_on = false;
+        if (!f_on && !g_on) break;
+        const int32_t k = k0 + lane;
         const int32_t col = cu + a.smaj * k;
-        if (col < 0 || col >= NU) break;
-        const int64_t rise = (int64_t)k * kS * lz;
-        if (top_all - rise <= F) break;  // no floor can beat F from here on
-        if (skip && (k - 1) % kBlock == 0) {
-            int64_t mh, mt;
-            if (!block_max(w, a, cu, cv, k, NU, NV, mh, mt)) break;
-            if (mh * kS * lmaj - rise <= F) {  // no column of the block can raise F
-                k += kBlock;
-                continue;
+        const bool in_col = col >= 0 && col < NU;
+        // rows floor(lmin * j / lmaj) of travel j = k - 1, k, k + 1
+        const int64_t qm = floor_div_est(lmin * (k - 1), lmaj, rcp_maj);
+        const int64_t qk = floor_div_est(lmin * k, lmaj, rcp_maj);
+        const int64_t qp = floor_div_est(lmin * (k + 1), lmaj, rcp_maj);
+        const int32_t f0 = cv + (int32_t)min(qm, qk), f1 = cv + 1 + (int32_t)max(qm, qk);
+        const int32_t g0 = cv + (int32_t)min(qm, qp), g1 = cv + 1 + (int32_t)max(qm, qp);
+        const bool f_ok = in_col && f0 >= 0 && f1 < NV;  // the whole F band in the grid
+        const bool g_ok = in_col && g1 >= 0 && g0 < NV;  // some of the G band in the grid
+        bool f_need = f_on, g_need = g_on;
+        if (skip && (f_need || g_need)) {
+            // the round's region: its columns and the rows of all its G bands
+            const int32_t rlo = max(__reduce_min_sync(full, g_ok ? g0 : 0x7FFFFFFF), 0);
+            const int32_t rhi = min(__reduce_max_sync(full, g_ok ? g1 : -1), NV - 1);
+            const int32_t ca = cu + a.smaj * k0, cb = cu + a.smaj * (k0 + 31);
+            const int32_t clo = max(min(ca, cb), 0), chi = min(max(ca, cb), NU - 1);
+            int32_t mh = -1, mt = -1;
+            if (rlo <= rhi && clo <= chi) {
+                const int32_t nu0 = clo >> 5, nv0 = rlo >> 5;
+                const int32_t nnu = (chi >> 5) - nu0 + 1, nnv = (rhi >> 5) - nv0 + 1;
+                if (lane < nnu * nnv) {
+                    const uint32_t n = node5_at(w, a, nu0 + lane % nnu, nv0 + lane / nnu);
+                    mh = (int32_t)(n & 0xFF);
+                    mt = (int32_t)((n >> 16) & 0xFF);
+                }
+                mh = __reduce_max_sync(full, mh);
+                mt = __reduce_max_sync(full, mt);
+            }
+            f_need = f_need && mh >= 0 &&
+                     (int64_t)mh * kS * lmaj - (int64_t)k0 * rise1 >= (int64_t)(F16 + 1) * unit;
+            g_need = g_need && mt >= 0 &&
+                     (int64_t)mt * kS * lmaj - (int64_t)(k0 - 1) * rise1 > (int64_t)G16 * unit;
+        }
+        if (f_need || g_need) {
+            int64_t m = 255, t = -1;
+            if (g_ok || f_ok)
+                for (int32_t r = max(g0, 0); r <= min(g1, NV - 1); ++r) {
+                    const uint32_t c = word_at(w, a, col, r);
+                    if (r >= f0 && r <= f1) m = min(m, (int64_t)(c & 0xFF));
+                    t = max(t, (int64_t)((c >> 16) & 0xFF));
+                }
+            if (f_need) {
+                const int32_t v = f_ok ? q_floor(m * kS * lmaj - (int64_t)k * rise1) : -1;
+                F16 = max(F16, __reduce_max_sync(full, v));
+            }
+            if (g_need) {
+                const int32_t v = g_ok ? q_ceil(t * kS * lmaj - (int64_t)(k - 1) * rise1) : 0;
+                G16 = max(G16, __reduce_max_sync(full, v));
             }
         }
-        const int64_t lo = min(lmin * (k - 1), lmin * k), hi = max(lmin * (k - 1), lmin * k);
-        const int32_t r0 = cv + (int32_t)floor_div64(lo, lmaj);
-        const int32_t r1 = cv + 1 + (int32_t)floor_div64(hi, lmaj);
-        if (r0 < 0 || r1 >= NV) break;  // the band drifts out of the grid for good
-        int64_t m = 255;
-        for (int32_t r = r0; r <= r1; ++r) m = min(m, (int64_t)(word_at(w, a, col, r) & 0xFF));
-        F = max(F, m * kS * lmaj - rise);
-        ++k;
-    }
-    // G: k = 0, the rows the ray can cross in its start column, strictly above
-    {
-        const int32_t r0 = cv + (int32_t)floor_div64(min((int64_t)0, lmin), lmaj);
-        const int32_t r1 = cv + 1 + (int32_t)floor_div64(max((int64_t)0, lmin), lmaj);
-        G = 0;
-        for (int32_t r = max(r0, 0); r <= min(r1, NV - 1); ++r)
-            G = max(G, ((int64_t)((word_at(w, a, cu, r) >> 16) & 0xFF) * kS + 1) * lmaj);
-    }
-    for (int32_t k = 1;;) {
-        const int32_t col = cu + a.smaj * k;
-        if (col < 0 || col >= NU) break;
-        const int64_t rise = (int64_t)(k - 1) * kS * lz;
-        if (top_all - rise <= G) break;  // no top can beat G from here on
-        if (skip && (k - 1) % kBlock == 0) {
-            int64_t mh, mt;
-            if (!block_max(w, a, cu, cv, k, NU, NV, mh, mt)) break;
-            if (mt * kS * lmaj - rise <= G) {  // no column of the block can raise G
-                k += kBlock;
-                continue;
-            }
-        }
-        const int64_t lo = min(lmin * (k - 1), lmin * (k + 1)),
-                      hi = max(lmin * (k - 1), lmin * (k + 1));
-        const int32_t r0 = cv + (int32_t)floor_div64(lo, lmaj);
-        const int32_t r1 = cv + 1 + (int32_t)floor_div64(hi, lmaj);
-        if (r1 < 0 || r0 >= NV) break;  // the band has left the grid: the ray has too
-        int64_t t = -1;
-        for (int32_t r = max(r0, 0); r <= min(r1, NV - 1); ++r)
-            t = max(t, (int64_t)((word_at(w, a, col, r) >> 16) & 0xFF));
-        if (t >= 0) G = max(G, t * kS * lmaj - rise);
-        ++k;
+        if (f_on && !__all_sync(full, f_ok)) f_on = false;
+        if (g_on && !__all_sync(full, g_ok)) g_on = false;
     }
 }
 
@@ -198,29 +211,28 @@ __device__ bool depends_on(const SunAxes &a, int32_t cu, int32_t cv, int32_t eu0
     return r1 >= ev0 && r0 < ev1;
 }
 
-// One thread per cell of the rectangle [x0, x1) x [y0, y1).  With ex1 > ex0,
-// only the cells whose bounds depend on the edited rectangle [ex0, ex1) x
-// [ey0, ey1) are recomputed (the others keep their words).
+// One warp per cell of the rectangle [x0, x1) x [y0, y1).  With edit.z >
+// edit.x, only the cells whose bounds depend on the edited rectangle
+// [edit.x, edit.z) x [edit.y, edit.w) are recomputed (the others keep theirs).
 __global__ void k_sun_bounds(const WorldDev w, uint32_t *fg, SunAxes a, int32_t x0, int32_t y0,
                              int32_t nx, uint32_t n, int4 edit, int32_t reach) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;  // warp-uniform
     const int32_t x = x0 + (int32_t)(i % (uint32_t)nx), y = y0 + (int32_t)(i / (uint32_t)nx);
     if (edit.z > edit.x) {
         const bool dep = a.x_major ? depends_on(a, x, y, edit.x, edit.y, edit.z, edit.w, reach)
                                    : depends_on(a, y, x, edit.y, edit.x, edit.w, edit.z, reach);
-        if (!dep) return;
+        if (!dep) return;  // warp-uniform
     }
-    int64_t F, G;
+    int32_t F16, G16;
     if (a.x_major)
-        bounds_of(w, a, x, y, w.W, w.H, F, G);
+        bounds_of_warp(w, a, x, y, w.W, w.H, lane, F16, G16);
     else
-        bounds_of(w, a, y, x, w.H, w.W, F, G);
-    const int64_t unit = (int64_t)a.lmaj << 8;  // 2^-8 world units, unscaled
-    int64_t f = floor_div64(F, unit), g = -floor_div64(-G, unit);
-    f = f < 0 ? 0 : (f > 65535 ? 65535 : f);
-    g = g < 0 ? 0 : (g > 65535 ? 65535 : g);
-    fg[(uint32_t)y * (uint32_t)w.W + (uint32_t)x] = (uint32_t)f | ((uint32_t)g << 16);
+        bounds_of_warp(w, a, y, x, w.H, w.W, lane, F16, G16);
+    if (lane == 0)
+        fg[(uint32_t)y * (uint32_t)w.W + (uint32_t)x] =
+            (uint32_t)max(F16, 0) | ((uint32_t)max(G16, 0) << 16);
 }
 
 SunAxes axes_of(const int32_t sun[3]) {
@@ -272,7 +284,7 @@ int sun_bounds(const WorldDev &w, uint32_t *fg, const int32_t sun[3], int32_t x0
     if (!sun_bounds_eligible(sun)) return -1;
     if (x1 <= x0 || y1 <= y0) return 0;
     const uint32_t nx = (uint32_t)(x1 - x0), n = nx * (uint32_t)(y1 - y0);
-    const uint32_t threads = 128, blocks = (n + threads - 1) / threads;
+    const uint32_t threads = 128, blocks = (n + threads / 32 - 1) / (threads / 32);
     k_sun_bounds<<<blocks, threads, 0, (cudaStream_t)stream>>>(w, fg, axes_of(sun), x0, y0,
                                                                 (int32_t)nx, n,
                                                                 make_int4(0, 0, 0, 0), 0);
@@ -289,7 +301,7 @@ int sun_bounds_repair(const WorldDev &w, uint32_t *fg, const int32_t sun[3], int
     const SunAxes a = axes_of(sun);
     const int32_t reach = (int32_t)(255 * (int64_t)a.lmaj / a.lz + 2);
     const uint32_t nx = (uint32_t)(r[2] - r[0]), n = nx * (uint32_t)(r[3] - r[1]);
-    const uint32_t threads = 128, blocks = (n + threads - 1) / threads;
+    const uint32_t threads = 128, blocks = (n + threads / 32 - 1) / (threads / 32);
     k_sun_bounds<<<blocks, threads, 0, (cudaStream_t)stream>>>(w, fg, a, r[0], r[1], (int32_t)nx,
                                                                 n, make_int4(x0, y0, x1, y1),
                                                                 reach);
