@@ -577,7 +577,10 @@ def test_host_staged_outputs_equal_device_outputs(hf, c1):
     for cells, cams, fields, sh in (
             (c1["cells"], c1["cams"], ("hit_cell", "layer", "face", "depth", "rgba", "shadow"), True),
             (synth.config_c3(scale=8)["cells"], synth.config_c3(scale=8)["cams"],
-             ("hit_cell", "depth", "rgba"), False)):
+             ("hit_cell", "depth", "rgba"), False),
+            # with shadow rays and every field
+            (synth.config_c3(scale=8)["cells"], synth.config_c3(scale=8)["cams"],
+             ("hit_cell", "layer", "face", "depth", "rgba", "shadow"), True)):
         ctx = _ctx(hf, cells)
         try:
             flags = hf.HF_SHADOWS if sh else 0
