@@ -365,7 +365,9 @@ def run_hf(args):
             x0, blk = xa, synth.pairify(full)
         return x0, y0, blk
 
-    def do_edit():
+    def do_edit(pre=None):
+        """One crater: drawn here (or given, drawn before a timed region), then
+        uploaded and repaired by hf_edit."""
         if ws > 1:
             # the replicas' one exchange step: rank 0 draws the crater, every
             # rank receives it and applies it to its own world
@@ -374,7 +376,7 @@ def run_hf(args):
             replicated_edit(draw_edit() if rank == 0 else None, cells, src=0, device="cuda",
                             apply=lambda x0, y0, b: hf.hf_edit(ctx, x0, y0, b))
             return
-        x0, y0, blk = draw_edit()
+        x0, y0, blk = pre if pre is not None else draw_edit()
         hf.hf_edit(ctx, x0, y0, blk)
         cells[y0:y0 + blk.shape[0], x0:x0 + blk.shape[1]] = blk
 
@@ -497,13 +499,16 @@ def run_hf(args):
 
         def e2e_time(via_host):
             ems = []
-            for i in range(max(1, min(3, args.steps))):
+            for i in range(max(1, min(5, args.steps))):
                 with torch.cuda.stream(stream):
                     flush.fill_(9)
+                # the crater is an input: drawn on the host before the timed region
+                # (on one GPU; under torchrun its broadcast is part of the step)
+                pre = draw_edit() if wl["edit"] and ws == 1 else None
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 if wl["edit"]:
-                    do_edit()
+                    do_edit(pre)
                 if via_host == "staged":
                     hf.hf_render(ctx, max_cams, host, sopts)
                 elif via_host:
