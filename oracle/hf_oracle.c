@@ -29,8 +29,9 @@
  * Shading is this project's own fixed choice (the paper names palette,
  * diffuse and shadow lookup but gives no constants): an 8-entry albedo table,
  * ambient 0.3 plus diffuse 0.7 times max(0, N.L) times sun visibility, with N
- * the hit face's normal.  Its parity is self-consistency only ("parity
- * unpinned" against the paper for colour).
+ * the hit face's normal.  Pinned against that stated rule by hand-derived
+ * colours for every face, lit, turned away and occluded
+ * (tests/golden/shading_faces.json); the paper prints no colours to pin it to.
  */
 #include <math.h>
 #include <pthread.h>
