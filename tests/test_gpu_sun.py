@@ -12,7 +12,10 @@ below F (occluded) or at or above G (lit) of its start cell.  Checked here:
   for suns without bounds (below the horizon, vertical, too low);
 * incremental repair after edits equals a fresh build bit for bit, and a
   render after edits equals the oracle on the edited world;
-* a change of sun rebuilds the bounds (renders alternate between two suns).
+* a change of sun rebuilds the bounds (renders alternate between two suns);
+* shadowed renders on two streams around an edit see the old and the new
+  world, and the native serving loop with shadow rays (lanes in flight,
+  craters in between) gives every request the oracle's image of its world.
 """
 
 import os
@@ -202,3 +205,73 @@ def test_bounds_cut_shadow_fetches(hf):
     per_shadow = with_b["shadow_fetches"] / with_b["shadow_rays"]
     assert per_shadow < 8.0, per_shadow
     assert without["shadow_fetches"] / without["shadow_rays"] > per_shadow
+
+
+def test_shadowed_renders_on_two_streams_around_an_edit(hf):
+    """A shadowed render on one stream, then an edit (a tall block whose
+    shadow reaches far upstream, so the bounds of many cells change), then a
+    shadowed render on another stream: the first sees the old world, the
+    second the new one, each equal to the oracle."""
+    import torch
+
+    cfg = synth.config_c1()
+    cells = cfg["cells"].copy()
+    cams = cfg["cams"]
+    ctx = hf.hf_create(cells)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    try:
+        a = hf.alloc_outputs(cams, shadows=True)
+        hf.hf_render(ctx, cams, a, hf.make_opts(flags=hf.HF_SHADOWS, stream=s1.cuda_stream))
+        blk = np.full((20, 20), synth.pack_cells(250, 0, 0, 3), np.uint32)
+        hf.hf_edit(ctx, 150, 90, blk)
+        cells[90:110, 150:170] = blk
+        b = hf.alloc_outputs(cams, shadows=True)
+        hf.hf_render(ctx, cams, b, hf.make_opts(flags=hf.HF_SHADOWS, stream=s2.cuda_stream))
+        hf.hf_sync(ctx)
+        torch.cuda.synchronize()
+        fix = lambda o: {k: (v.cpu().numpy().view(np.uint32) if k in ("hit_cell", "rgba")
+                             else v.cpu().numpy()) for k, v in o.items()}
+        compare(fix(a[0]), oracle.render(cfg["cells"], cams[0], shadows=True), shadows=True,
+                what="stream 1 before the edit")
+        compare(fix(b[0]), oracle.render(cells, cams[0], shadows=True), shadows=True,
+                what="stream 2 after the edit")
+        fa, fb = fix(a[0]), fix(b[0])
+        assert any((fa[k] != fb[k]).any() for k in ("shadow", "hit_cell"))  # the edit shows
+    finally:
+        hf.hf_destroy(ctx)
+
+
+def test_native_serving_loop_with_shadow_rays(hf):
+    """hf_serve_replay with HF_SHADOWS: renders on several lanes in flight,
+    crater edits repairing the shadow bounds in between; every served image
+    equals the oracle on the world with exactly the edits before it."""
+    import torch
+
+    cells, _ = synth.make_grid(384, 384, seed=23, slab_frac=0.3, n_walls=16)
+    records = synth.poisson_requests(cells, 40, rate=2e4, seed=4, edit_every=5,
+                                     resolutions=((96, 64), (160, 90), (64, 48)))
+    outs = [None if r["kind"] == "edit" else hf.alloc_outputs(np.array([r["cam"]]),
+                                                              shadows=True)[0]
+            for r in records]
+    ctx = hf.hf_create(cells)
+    try:
+        res = hf.hf_serve_replay(ctx, records, lanes=4, max_batch=3, output_budget=64 << 20,
+                                 flags=hf.HF_SHADOWS, outputs=outs)
+        hf.hf_sync(ctx)
+        torch.cuda.synchronize()
+    finally:
+        hf.hf_destroy(ctx)
+    assert len(set(res["batch"][res["batch"] != 0xFFFFFFFF])) > 3
+    world = cells.copy()
+    checked = 0
+    for i, rec in enumerate(records):
+        if rec["kind"] == "edit":
+            x0, y0, blk = rec["edit"]
+            world[y0:y0 + blk.shape[0], x0:x0 + blk.shape[1]] = blk
+            continue
+        g = {k: (v.cpu().numpy().view(np.uint32) if k in ("hit_cell", "rgba") else v.cpu().numpy())
+             for k, v in outs[i].items()}
+        compare(g, oracle.render(world, rec["cam"], shadows=True), shadows=True,
+                what="served request %d" % i)
+        checked += 1
+    assert checked == sum(r["kind"] == "render" for r in records)
