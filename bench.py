@@ -578,7 +578,9 @@ def run_hf(args):
                                       mip_start, info["sm_count"],
                                       (ck or {}).get("sm_mhz") or _peak_sm_mhz()),
         "fetches_per_ray": (st["node_fetches"] + st["cell_fetches"]) / max(rays, 1),
-        "gpu_launches": args.steps * ((2 if wl["edit"] else 1)),
+        # per step: the render, and for a crater the pyramid repair plus, once
+        # the shadow bounds exist (shadow rays toward the default sun), their repair
+        "gpu_launches": args.steps * (1 + ((2 if wl["shadows"] else 1) if wl["edit"] else 0)),
         "clocks": ck,
         "e2e": e2e,
     }
