@@ -18,7 +18,8 @@ import numpy as np
 
 from . import HF_HOST_OUTPUTS, HF_MIP_AUTO, HF_SHADOWS, hf_info, hf_render, hf_sync, make_opts
 
-DEFAULT_TILES = ((8, 4), (4, 8), (16, 2), (8, 8), (16, 4), (8, 16), (4, 16), (4, 32), (8, 32))
+DEFAULT_TILES = ((8, 4), (4, 8), (16, 2), (8, 8), (16, 4), (8, 16), (4, 16), (4, 32), (8, 32),
+                 (4, 64))
 # With HF_HOST_OUTPUTS the kernel's stores cross the host link, where a warp
 # store of a short row piece costs nearly as much as a whole line: tiles whose
 # rows are 32 pixels or wider keep those stores long.
