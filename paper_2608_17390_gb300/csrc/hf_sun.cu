@@ -33,10 +33,12 @@
 // role -- sun visibility precomputed once per frame -- but approximately;
 // these bounds only ever decide cases they prove.
 //
-// Only suns that rise (Lz > 0) and are not vertical have bounds.  An edit of a
-// rectangle changes the bounds of the cells upstream of it (against L) within
-// the distance over which a ray can rise by 255 units: sun_bounds_region gives
-// that rectangle, and the same kernel recomputes it.
+// Only suns that rise (Lz > 0), are not vertical and clear the 255-unit
+// height range within kSunMaxReach columns have bounds.  An edit of a
+// rectangle changes the bounds of cells upstream of it (against L), within the
+// distance over which a ray rises by 255 units: sun_bounds_region gives the
+// rectangle that holds them, and sun_bounds_repair recomputes, inside it, the
+// cells whose bands reach the edited rectangle (a parallelogram along L).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -48,12 +50,6 @@ namespace hf {
 namespace {
 
 constexpr int64_t kS = 1 << kShift;
-
-__device__ __forceinline__ int64_t floor_div64(int64_t a, int64_t b) {  // b > 0
-    int64_t q = a / b;
-    if ((a % b) != 0 && a < 0) q -= 1;
-    return q;
-}
 
 // Node-form word of level-0 cell (x, y), either storage (top = byte 2, floor = byte 0).
 __device__ __forceinline__ uint32_t cell_node(const WorldDev &w, int32_t x, int32_t y) {
@@ -206,8 +202,10 @@ __device__ bool depends_on(const SunAxes &a, int32_t cu, int32_t cv, int32_t eu0
     kb = min(kb, reach);
     if (ka > kb) return false;
     const int64_t lmin = a.lmin, lmaj = a.lmaj;
+    const float rcp_maj = 1.0f / (float)lmaj;
     const int64_t lo = min(lmin * (ka - 1), lmin * (kb + 1)), hi = max(lmin * (ka - 1), lmin * (kb + 1));
-    const int32_t r0 = cv + (int32_t)floor_div64(lo, lmaj), r1 = cv + 1 + (int32_t)floor_div64(hi, lmaj);
+    const int32_t r0 = cv + (int32_t)floor_div_est(lo, lmaj, rcp_maj);
+    const int32_t r1 = cv + 1 + (int32_t)floor_div_est(hi, lmaj, rcp_maj);
     return r1 >= ev0 && r0 < ev1;
 }
 
