@@ -870,7 +870,7 @@ static int finish_batch(hf_ctx *c, Batch &b, bool sync) {
 static int render_host_staged(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_outputs *outs,
                               const hf_render_opts &o) {
 #ifndef HF_STAGE_CHUNKS
-#define HF_STAGE_CHUNKS 16  // measured: 4 / 8 / 16 / 32 chunks
+#define HF_STAGE_CHUNKS 24  // measured: 4 / 8 / 12 / 16 / 24 / 32 / 48 chunks
 #endif
 #ifndef HF_STAGE_BUFFERS
 #define HF_STAGE_BUFFERS 4  // measured: 2 / 3 / 4 buffers
