@@ -33,7 +33,7 @@ namespace hf {
 namespace {
 
 #ifndef HF_TRACE_MIN_BLOCKS
-#define HF_TRACE_MIN_BLOCKS 6  // resident blocks per SM asked of the register allocator (<= 80 registers)
+#define HF_TRACE_MIN_BLOCKS 3  // resident 256-thread blocks per SM asked of the register allocator (<= 85 registers)
 #endif
 
 __constant__ float c_albedo[8][3] = HF_ALBEDO_TABLE;
