@@ -73,13 +73,14 @@ extern "C" {
 #define HF_NOWAIT 32u /* return HF_E_BUSY instead of waiting for a free render slot */
 #define HF_SCATTER_RAW 128u /* hf_render_scatter: leave the packed words in hit_cell, no resolve */
 #define HF_HOST_STAGED 256u /* the output buffers are pinned HOST memory: the library renders
-                               chunks of consecutive cameras (about 1/16 of the pixels each,
-                               then halving chunks for the last eighth) into its own device
-                               staging (four buffers of the largest chunk, allocated on first
-                               use) and copies each finished chunk back on a copy stream while
-                               later chunks render; cameras whose host buffers of one field lie
-                               back to back share one copy (hf_render only; not with
-                               HF_HOST_OUTPUTS, HF_PLAIN or HF_NOWAIT) */
+                               the batch in chunks of equal pixel counts (cameras split into
+                               row bands, each rendered as a camera of its own with the same
+                               pixel rays) into its own device staging (four buffers of the
+                               largest chunk, allocated on first use) and copies each finished
+                               chunk back on a copy stream while later chunks render; bands
+                               whose host buffers of one field lie back to back share one
+                               copy (hf_render only; not with HF_HOST_OUTPUTS, HF_PLAIN or
+                               HF_NOWAIT) */
 #define HF_HOST_OUTPUTS 64u /* the output buffers are pinned HOST memory (cudaHostAlloc or
                                cudaHostRegister): the kernel writes the results there itself,
                                over the host link, with no separate copy (hf_render only) */
@@ -252,13 +253,13 @@ int hf_render(hf_ctx *ctx, const hf_camera *cams, uint32_t n, const hf_outputs *
  * Scratch: one statically allocated device array of about 28 KiB (batch
  * header with the tile counter, camera table, status word) that every GPU
  * loading this library holds until the process exits.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress) once;
- * make that first call before any stream capture.  All calls share the array
- * and it keeps the last call's contents; each call rewrites what must start
- * at zero.  Calls whose GPU work overlaps (from several threads or contexts on
- * one device) race on the array; calls ordered on one stream do not.  The
- * camera table is copied from pageable host memory, so the call waits for
- * earlier work on the context's stream before returning.
+ * device looks up that array's device address (cudaGetSymbolAddress) once.
+ * All calls share the array and it keeps the last call's contents; each
+ * call rewrites what must start at zero.  Calls whose GPU work overlaps
+ * (from several threads or contexts on one device) race on the array; calls
+ * ordered on one stream do not.  The camera table is copied from pageable
+ * host memory, so the call waits for earlier work on the context's stream
+ * before returning.
  * Errors: HF_E_INVALID_ARG (null, n > HF_NOALLOC_MAX_CAMERAS, invalid camera,
  * tile shape, stream or flag), HF_E_CUDA, and with HF_SYNC HF_E_STEP_LIMIT. */
 #define HF_NOALLOC_MAX_CAMERAS 256u
