@@ -455,22 +455,31 @@ def run_hf(args):
     rays_step = sum(n_rays(step_cams(args.warmup + i)) for i in range(args.steps)) / args.steps
     value = rays_step * args.steps * ws / (total_ms / 1e3)
 
-    # plain: one launch per camera, same accuracy, same stream, L2 flushed
-    plain = None
+    # plain: one launch per camera, same accuracy, same stream, L2 flushed;
+    # its tile shape is chosen for it (one render per candidate), since the
+    # batched kernel's choice need not suit one launch per camera
+    plain = plain_tile = None
     if not args.no_plain:
-        popts = hf.make_opts(flags=flags | hf.HF_PLAIN, mip_start=mip_start, tile_w=tile_w,
-                             tile_h=tile_h)
-        pms = []
-        for i in range(max(1, min(3, args.steps))):
-            with torch.cuda.stream(stream):
-                flush.fill_(7)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            hf.hf_render(ctx, max_cams, outs[:len(max_cams)], popts)
-            b.record(stream)
-            hf.hf_sync(ctx)
-            pms.append(a.elapsed_time(b))
-        plain = n_rays(max_cams) / (float(np.median(pms)) / 1e3)
+        def plain_ms(tw, th, reps):
+            popts = hf.make_opts(flags=flags | hf.HF_PLAIN, mip_start=mip_start, tile_w=tw,
+                                 tile_h=th)
+            pms = []
+            for i in range(reps):
+                with torch.cuda.stream(stream):
+                    flush.fill_(7)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                hf.hf_render(ctx, max_cams, outs[:len(max_cams)], popts)
+                b.record(stream)
+                hf.hf_sync(ctx)
+                pms.append(a.elapsed_time(b))
+            return float(np.median(pms))
+
+        cands = [(tile_w, tile_h)] + [t for t in ((8, 4), (4, 8), (8, 8), (4, 16), (8, 16), (4, 32),
+                                                   (8, 32), (4, 64)) if t != (tile_w, tile_h)]
+        plain_ms(*cands[0], 1)  # warm-up
+        plain_tile = min(cands, key=lambda t: plain_ms(t[0], t[1], 1))
+        plain = n_rays(max_cams) / (plain_ms(*plain_tile, max(1, min(3, args.steps))) / 1e3)
 
     # end to end through the public API with host buffers: host camera records
     # and edit cells in, every output field back in pinned host memory, timed
@@ -562,6 +571,7 @@ def run_hf(args):
                    "autotuned": tuned,
                    "world_bytes": info["cell_bytes"] + info["pyramid_bytes"]},
         "plain_rays_per_s": plain,
+        "plain_tile": ("%dx%d" % plain_tile) if plain_tile else None,
         "batched_over_plain": (value / ws / plain) if plain else None,
         "render_ms": r_ms,
         "pyramid_build_ms": build_ms,

@@ -73,9 +73,9 @@ extern "C" {
 #define HF_NOWAIT 32u /* return HF_E_BUSY instead of waiting for a free render slot */
 #define HF_SCATTER_RAW 128u /* hf_render_scatter: leave the packed words in hit_cell, no resolve */
 #define HF_HOST_STAGED 256u /* the output buffers are pinned HOST memory: the library renders
-                               the batch in chunks of equal pixel counts (cameras split into
-                               row bands, each rendered as a camera of its own with the same
-                               pixel rays) into its own device staging (four buffers of the
+                               the batch in chunks of equal pixel counts (at least 2^19
+                               pixels; cameras split into row bands, each rendered as a camera
+                               of its own with the same pixel rays) into its own device staging (four buffers of the
                                largest chunk, allocated on first use) and copies each finished
                                chunk back on a copy stream while later chunks render; bands
                                whose host buffers of one field lie back to back share one

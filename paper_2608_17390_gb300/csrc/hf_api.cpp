@@ -862,20 +862,32 @@ static int finish_batch(hf_ctx *c, Batch &b, bool sync) {
     return HF_OK;
 }
 
-// HF_HOST_STAGED: render the cameras in about kStageChunks contiguous chunks of
-// similar pixel counts into a ring of kBuffers device staging buffers, and
-// stream each finished chunk to the caller's pinned host buffers on the copy
-// stream while later chunks render.  The render stream waits for the last
-// copies.
+// HF_HOST_STAGED: render the cameras in kStageChunks chunks of equal pixel
+// counts (no smaller than kMinChunkPx, as each chunk costs a launch and a few
+// copies) into a ring of kBuffers device staging buffers, and stream each
+// finished chunk to the caller's pinned host buffers on the copy stream while
+// later chunks render.  The render stream waits for the last copies.
+//
+// A chunk is a run of pieces: row bands of the cameras, in order.  Rows
+// [row0, row0 + rows) of a camera form a camera of their own, with the same
+// origin, right and up vectors, `rows` rows, and fwd moved to the band's
+// middle row,
+//   fwd' = fwd + (h - rows - 2 row0) up,
+// so that each of its pixels has the same integer direction, and therefore
+// the same result, as in the whole camera.  fwd' lies between fwd - (h-1) up
+// and fwd + (h-1) up, each the mean of two corner directions, so the band is
+// valid whenever the camera is.  So one large camera streams too: its copies
+// start after its first band.
 static int render_host_staged(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_outputs *outs,
                               const hf_render_opts &o) {
 #ifndef HF_STAGE_CHUNKS
-#define HF_STAGE_CHUNKS 24  // measured: 4 / 8 / 12 / 16 / 24 / 32 / 48 chunks
+#define HF_STAGE_CHUNKS 24  // measured: 8 / 12 / 16 / 24 / 32 / 48 / 96 / 192 chunks
 #endif
 #ifndef HF_STAGE_BUFFERS
 #define HF_STAGE_BUFFERS 4  // measured: 2 / 3 / 4 buffers
 #endif
     constexpr uint32_t kStageChunks = HF_STAGE_CHUNKS;
+    constexpr uint64_t kMinChunkPx = 1u << 19;  // ~40 us of render or copy
     constexpr int kBuffers = HF_STAGE_BUFFERS;
     constexpr size_t kAlign = 256;
     const bool shadows = (o.flags & HF_SHADOWS) != 0;
@@ -915,35 +927,39 @@ static int render_host_staged(hf_ctx *c, const hf_camera *cams, uint32_t n, cons
             if (a.type != cudaMemoryTypeHost) return HF_E_INVALID_ARG;  // pinned host memory only
         }
     }
-    // chunks of consecutive cameras: about total / kStageChunks pixels each
-    // until an eighth of the pixels is left, then halving chunks (down to
-    // total / 128), so that the last copy, which nothing overlaps, is small
-    // (cameras ordered largest first make those chunks fine-grained)
-    std::vector<uint32_t> first;
+    struct Piece {
+        uint32_t cam, row0, rows;
+    };
+    std::vector<Piece> pieces;
+    std::vector<uint32_t> first;  // chunk k is pieces[first[k], first[k + 1])
     {
-        uint64_t done = 0, acc = 0;
+        const uint64_t target = std::max((total_px + kStageChunks - 1) / kStageChunks, kMinChunkPx);
+        uint64_t acc = 0;
         first.push_back(0);
         for (uint32_t i = 0; i < n; ++i) {
-            acc += (uint64_t)cams[i].w * cams[i].h;
-            const uint64_t left = total_px - done;  // pixels from this chunk's first camera on
-            const uint64_t target = left > total_px / 8
-                                        ? (total_px + kStageChunks - 1) / kStageChunks
-                                        : std::max<uint64_t>(left / 2, total_px / 128);
-            if (acc >= target && i + 1 < n) {
-                first.push_back(i + 1);
-                done += acc;
-                acc = 0;
+            const uint32_t w = cams[i].w, h = cams[i].h;
+            for (uint32_t row = 0; row < h;) {
+                const uint64_t want = (target - acc + w - 1) / w;  // rows that fill the chunk
+                const uint32_t rows = (uint32_t)std::min<uint64_t>(h - row, want);
+                pieces.push_back({i, row, rows});
+                row += rows;
+                acc += (uint64_t)rows * w;
+                if (acc >= target) {
+                    first.push_back((uint32_t)pieces.size());
+                    acc = 0;
+                }
             }
         }
-        first.push_back(n);
+        if (first.back() != pieces.size()) first.push_back((uint32_t)pieces.size());
     }
-    // staging layout of a chunk: field by field, the chunk's cameras back to
-    // back (so that cameras whose host buffers are adjacent need one copy)
-    auto chunk_stage_bytes = [&](uint32_t i0, uint32_t i1) {
+    auto piece_px = [&](const Piece &q) { return (size_t)cams[q.cam].w * q.rows; };
+    // staging layout of a chunk: field by field, the chunk's pieces back to
+    // back (so that pieces whose host buffers are adjacent need one copy)
+    auto chunk_stage_bytes = [&](uint32_t k0, uint32_t k1) {
         size_t b = 0;
         for (int f = 0; f < 6; ++f) {
             size_t fb = 0;
-            for (uint32_t i = i0; i < i1; ++i) fb += field_bytes(outs[i], f) * cams[i].w * cams[i].h;
+            for (uint32_t k = k0; k < k1; ++k) fb += field_bytes(outs[pieces[k].cam], f) * piece_px(pieces[k]);
             b += (fb + kAlign - 1) & ~(kAlign - 1);
         }
         return b;
@@ -981,7 +997,9 @@ static int render_host_staged(hf_ctx *c, const hf_camera *cams, uint32_t n, cons
     hf_render_opts inner = o;
     inner.flags &= ~(HF_HOST_STAGED | HF_HOST_OUTPUTS | HF_SYNC);
     inner.cuda_stream = s;
+    std::vector<hf_camera> band;
     std::vector<hf_outputs> dev;
+    std::vector<const char *> srcs;  // staging of (piece, field), for the copies
     // the second render stream starts after the work already on the caller's
     const cudaStream_t rs[2] = {s, c->render2};
     CK(cudaEventRecord(c->stage_start, s));
@@ -991,16 +1009,27 @@ static int render_host_staged(hf_ctx *c, const hf_camera *cams, uint32_t n, cons
         const cudaStream_t ks = rs[k & 1];
         if (c->stage_busy[b]) CK(cudaStreamWaitEvent(ks, c->stage_free[b], 0));
         char *base = c->d_hstage + b * c->hstage_half;
-        const uint32_t i0 = first[k], i1 = first[k + 1];
-        dev.assign(i1 - i0, hf_outputs{});
+        const uint32_t k0 = first[k], k1 = first[k + 1];
+        band.assign(k1 - k0, hf_camera{});
+        dev.assign(k1 - k0, hf_outputs{});
+        srcs.assign((size_t)(k1 - k0) * 6, nullptr);
+        for (uint32_t q = k0; q < k1; ++q) {
+            const Piece &pc = pieces[q];
+            hf_camera &bc = band[q - k0];
+            bc = cams[pc.cam];
+            const int64_t shift = (int64_t)bc.h - pc.rows - 2 * (int64_t)pc.row0;
+            for (int i = 0; i < 3; ++i) bc.fwd[i] = (int32_t)(bc.fwd[i] + shift * bc.up[i]);
+            bc.h = pc.rows;
+        }
         size_t off = 0;
         for (int f = 0; f < 6; ++f) {
-            for (uint32_t i = i0; i < i1; ++i) {
-                const size_t fb = field_bytes(outs[i], f) * cams[i].w * cams[i].h;
+            for (uint32_t q = k0; q < k1; ++q) {
+                const size_t fb = field_bytes(outs[pieces[q].cam], f) * piece_px(pieces[q]);
                 if (!fb) continue;
                 void *slot = base + off;
                 off += fb;
-                hf_outputs &d = dev[i - i0];
+                srcs[(size_t)(q - k0) * 6 + f] = static_cast<const char *>(slot);
+                hf_outputs &d = dev[q - k0];
                 switch (f) {
                     case 0: d.hit_cell = (uint32_t *)slot; break;
                     case 1: d.layer = (uint8_t *)slot; break;
@@ -1013,26 +1042,29 @@ static int render_host_staged(hf_ctx *c, const hf_camera *cams, uint32_t n, cons
             off = (off + kAlign - 1) & ~(kAlign - 1);
         }
         inner.cuda_stream = ks;
-        const int rc = hf_render(c, cams + i0, i1 - i0, dev.data(), &inner);
+        const int rc = hf_render(c, band.data(), k1 - k0, dev.data(), &inner);
         if (rc != HF_OK) return rc;
         CK(cudaEventRecord(c->stage_ready[b], ks));
         CK(cudaStreamWaitEvent(c->copy_stream, c->stage_ready[b], 0));
-        // one copy per run of cameras whose host buffers of this field are
+        // one copy per run of pieces whose host buffers of this field are
         // adjacent (their staging is adjacent by construction)
         for (int f = 0; f < 6; ++f) {
             char *run_dst = nullptr;
             const char *run_src = nullptr;
             size_t run_bytes = 0;
-            for (uint32_t i = i0; i <= i1; ++i) {
+            for (uint32_t q = k0; q <= k1; ++q) {
                 size_t fb = 0;
                 char *dst = nullptr;
                 const char *src = nullptr;
-                if (i < i1) {
-                    fb = field_bytes(outs[i], f) * cams[i].w * cams[i].h;
-                    dst = static_cast<char *>(field_ptr(outs[i], f));
-                    const hf_outputs &d = dev[i - i0];
-                    const void *srcs[6] = {d.hit_cell, d.layer, d.face, d.depth, d.rgba, d.shadow};
-                    src = static_cast<const char *>(srcs[f]);
+                if (q < k1) {
+                    const Piece &pc = pieces[q];
+                    const size_t eb = field_bytes(outs[pc.cam], f);
+                    fb = eb * piece_px(pc);
+                    if (fb) {
+                        dst = static_cast<char *>(field_ptr(outs[pc.cam], f)) +
+                              eb * cams[pc.cam].w * pc.row0;
+                        src = srcs[(size_t)(q - k0) * 6 + f];
+                    }
                 }
                 if (run_bytes && fb && dst == run_dst + run_bytes && src == run_src + run_bytes) {
                     run_bytes += fb;

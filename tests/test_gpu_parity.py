@@ -603,3 +603,36 @@ def test_host_staged_outputs_equal_device_outputs(hf, c1):
             hf.hf_sync(ctx)
         finally:
             hf.hf_destroy(ctx)
+
+
+def _window(cam, x0, y0, w, h):
+    """Pixels [x0, x0 + w) x [y0, y0 + h) of a camera, as a camera of their own
+    (the same rays: fwd moved to the window's centre)."""
+    o, f, r, u, w0, h0 = cam
+    a, b = 2 * x0 + w - w0, h0 - h - 2 * y0
+    return (o, tuple(f[i] + a * r[i] + b * u[i] for i in range(3)), r, u, w, h)
+
+
+def test_host_staged_row_bands_equal_the_oracle(hf, c1):
+    """HF_HOST_STAGED renders chunks of equal pixel counts (here about ten),
+    splitting cameras into row bands: a batch of cameras one pixel wide or
+    high, of odd sizes, and two far larger than a chunk equals the oracle
+    pixel for pixel."""
+    cells = c1["cells"]
+    base = synth.pose_to_camera(60.5, 80.25, 120.0, 30.0, -30.0, 70.0, 2560, 1600)
+    wins = [(0, 0, 1, 1), (5, 3, 1, 37), (100, 200, 45, 1), (7, 9, 33, 17), (0, 0, 2560, 1600),
+            (300, 10, 7, 200), (1600, 1200, 2, 2), (100, 50, 1000, 777)]
+    cams = synth.camera_array([_window(base, *wn) for wn in wins])
+    ctx = _ctx(hf, cells)
+    try:
+        for rep in range(2):
+            host = hf.alloc_outputs(cams, device="pinned", shadows=True)
+            hf.hf_render(ctx, cams, host,
+                         hf.make_opts(flags=hf.HF_SHADOWS | hf.HF_HOST_STAGED | hf.HF_SYNC))
+            for i, c in enumerate(cams):
+                g = {k: t.numpy().view(np.uint32) if k in ("hit_cell", "rgba") else t.numpy()
+                     for k, t in host[i].items()}
+                compare(g, oracle.render(cells, c, shadows=True, nthreads=NT), shadows=True,
+                        what="rep %d window %s" % (rep, wins[i]))
+    finally:
+        hf.hf_destroy(ctx)

@@ -8,8 +8,9 @@ below F (occluded) or at or above G (lit) of its start cell.  Checked here:
   extents the start-cell rule gives) at exactly height F and G are traced by
   the oracle, which must find them occluded and lit;
 * shadowed renders equal the oracle for suns along every octant, along an
-  axis, exactly diagonal, steep and near the lowest sun that has bounds, and
-  for suns without bounds (below the horizon, vertical, too low);
+  axis, exactly diagonal, steep, near and at the lowest sun that has bounds
+  (a reach of 1024 columns), and for suns without bounds (below the horizon,
+  vertical, too low, and one column of reach too low);
 * incremental repair after edits equals a fresh build bit for bit, and a
   render after edits equals the oracle on the edited world;
 * a change of sun rebuilds the bounds (renders alternate between two suns);
@@ -41,11 +42,13 @@ SUNS = [
     (0, -400000, 300000),         # along -y
     (-250000, -250000, 400000),   # diagonal, steep
     (400000, 100000, 100000),     # low: close to the lowest sun with bounds
+    (401000, 37000, 100000),      # the lowest: floor(255 * 4.01) + 2 = 1024 columns of reach
 ]
 NO_BOUNDS = [
     (300000, 100000, -50000),     # below the horizon
     (0, 0, 400000),               # vertical
     (400000, 0, 20000),           # too low: rays need > 1024 cells to clear 255
+    (401400, 37000, 100000),      # just too low: floor(255 * 4.014) + 2 = 1025 columns
 ]
 
 
