@@ -27,6 +27,7 @@ constexpr int kSlots = 8;
 constexpr size_t kScratchAlign = 4096;
 constexpr int kMaxGraphsPerSlot = 16;
 constexpr int32_t kLimit21 = 1 << 21;
+constexpr size_t kPrefetchBytes = 32u << 20;  // world levels warmed in L2 per render launch
 constexpr int32_t kDefaultSun[3] = {321060, -321060, 262144};
 
 struct GraphKey {
@@ -840,6 +841,13 @@ static int prepare_batch(hf_ctx *c, const hf_camera *cams, uint32_t n, const hf_
     }
     std::memset(&b.p, 0, sizeof(b.p));
     b.p.world = c->wd;
+    {  // the levels the trace kernels warm in L2: from the finest level whose
+       // tail of the world fits kPrefetchBytes (the whole of a small world)
+        uint32_t k = 0;
+        while (k < (uint32_t)c->L && (c->world_words - c->wd.off[k]) * 4 > kPrefetchBytes) ++k;
+        b.p.prefetch = c->wd.base + c->wd.off[k];
+        b.p.prefetch_lines = (uint32_t)(((c->world_words - c->wd.off[k]) * 4 + 127) / 128);
+    }
     b.p.hdr = (hf::BatchHeader *)s.d_scratch;
     b.p.cams = (const hf::CamDev *)((char *)s.d_scratch + sizeof(hf::BatchHeader));
     b.p.status = c->d_status;

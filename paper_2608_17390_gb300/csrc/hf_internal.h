@@ -136,6 +136,8 @@ struct RenderParams {
     int32_t sun[3];
     float sun_n[3];                // sun / |sun|
     const uint32_t *sun_bounds;    // per-cell shadow bounds for `sun` (hf_sun.cu), or null
+    const uint32_t *prefetch;      // start of the world levels the trace kernels warm in L2
+    uint32_t prefetch_lines;       // 128-byte lines from `prefetch` (0: none)
 };
 
 // Parameters of the fixed-step comparison marcher (hf_march.cu).

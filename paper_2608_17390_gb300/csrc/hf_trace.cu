@@ -536,6 +536,16 @@ __device__ __forceinline__ void trace_tile(const RenderParams &p, const LevelDev
     }
 }
 
+// Asks L2 for the world's coarse levels (all of a small world) as a launch
+// starts, spread over all its threads.  A ray's fetches form one dependent
+// chain, so a short render of a world that is not in L2 would otherwise wait
+// on DRAM at every step of every ray.
+__device__ __forceinline__ void prefetch_world(const RenderParams &p) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < p.prefetch_lines; i += stride)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(p.prefetch + (size_t)i * 32));
+}
+
 // stride of level 0 is its width in cells also for paired texels (whose rows
 // then hold stride / 2 words)
 __device__ __forceinline__ void fill_levels(LevelDev *s_lv, const WorldDev &w) {
@@ -565,6 +575,7 @@ __global__ void __launch_bounds__(kThreads, HF_TRACE_MIN_BLOCKS) k_trace_batched
     __shared__ LevelDev s_lv[kMaxLevels + 1];
     const uint32_t n = p.hdr->n_cams;
     const uint32_t total = p.hdr->total_tiles;
+    prefetch_world(p);
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) s_base[i] = p.cams[i].tile_base;
     fill_levels(s_lv, p.world);
     __syncthreads();
@@ -597,6 +608,7 @@ __global__ void __launch_bounds__(kThreads, HF_TRACE_MIN_BLOCKS)
                   uint32_t n_tiles) {
     __shared__ LevelDev s_lv[kMaxLevels + 1];
     __shared__ CamDev s_cam[kThreads / 32];
+    prefetch_world(p);
     fill_levels(s_lv, p.world);
     __syncthreads();
     const uint32_t t = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
