@@ -648,7 +648,7 @@ static int ensure_sun_bounds(hf_ctx *c, const int32_t sun[3], const uint32_t **o
     }
     CK(cudaSetDevice(c->device));
     if (!c->d_sun) {
-        if (cudaMalloc(&c->d_sun, (size_t)c->W * c->H * sizeof(uint32_t)) != cudaSuccess) {
+        if (cudaMalloc(&c->d_sun, hf::sun_bounds_bytes((int32_t)c->W, (int32_t)c->H)) != cudaSuccess) {
             (void)cudaGetLastError();
             c->d_sun = nullptr;
             return HF_E_OOM;

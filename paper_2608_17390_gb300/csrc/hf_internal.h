@@ -211,6 +211,10 @@ int ctx_view(const ::hf_ctx *ctx, CtxView *out);
 // clear the 255-unit height range within kSunMaxReach cells.
 constexpr int64_t kSunMaxReach = 1024;
 bool sun_bounds_eligible(const int32_t sun[3]);
+// Bytes of the bounds buffer of a W x H grid: the W * H words, then a table
+// of the sun's row offsets per column of travel that the build fills and the
+// repair reads.
+size_t sun_bounds_bytes(int32_t W, int32_t H);
 // Recompute the bounds of the cells of [x0, x1) x [y0, y1) from the cells.
 int sun_bounds(const WorldDev &w, uint32_t *bounds, const int32_t sun[3], int32_t x0, int32_t y0,
                int32_t x1, int32_t y1, void *stream);

@@ -39,6 +39,9 @@
 // distance over which a ray rises by 255 units: sun_bounds_region gives the
 // rectangle that holds them, and sun_bounds_repair recomputes, inside it, the
 // cells whose bands reach the edited rectangle (a parallelogram along L).
+// The band rows depend on the column of travel only, not on the cell: a full
+// build first tabulates them (k_sun_rows) after the bounds words, and the
+// build and later repairs read the table instead of dividing.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -50,6 +53,22 @@ namespace hf {
 namespace {
 
 constexpr int64_t kS = 1 << kShift;
+
+// Row-offset table after the bounds words: entry j + 1 holds floor(lmin j /
+// lmaj), the minor-axis rows a ray has crossed after j columns of major
+// travel, for j = -1 .. kRowTable - 2.  A bound reads columns up to K + 63
+// (K <= kSunMaxReach), so every lookup is in range; one outside it would
+// fall back to the float-estimated division.
+constexpr int kRowTable = (int)kSunMaxReach + 128;
+
+__global__ void k_sun_rows(int32_t *q, int64_t lmin, int64_t lmaj) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kRowTable) return;
+    const int64_t a = lmin * (i - 1);
+    int64_t d = a / lmaj;  // once per sun: the exact division is affordable here
+    if (a % lmaj != 0 && a < 0) d -= 1;
+    q[i] = (int32_t)d;
+}
 
 // Node-form word of level-0 cell (x, y), either storage (top = byte 2, floor = byte 0).
 __device__ __forceinline__ uint32_t cell_node(const WorldDev &w, int32_t x, int32_t y) {
@@ -88,6 +107,13 @@ __device__ __forceinline__ uint32_t node5_at(const WorldDev &w, const SunAxes &a
     return __ldg(w.base + w.off[5] + (uint32_t)y * w.stride[5] + (uint32_t)x);
 }
 
+// floor(lmin * j / lmaj) from the row-offset table.
+__device__ __forceinline__ int64_t rows_after(const SunAxes &a, const int32_t *rq, int32_t j,
+                                              float rcp_maj) {
+    if ((uint32_t)(j + 1) < (uint32_t)kRowTable) return __ldg(rq + j + 1);
+    return floor_div_est((int64_t)a.lmin * j, a.lmaj, rcp_maj);
+}
+
 // F and G of the cell at major / minor coordinates (cu, cv), rounded to the
 // stored units (F down, G up, 2^-8 world units), computed by the 32 lanes of a
 // warp: lane l takes column k = k0 + l of each round of 32 (its band's lowest
@@ -99,8 +125,9 @@ __device__ __forceinline__ uint32_t node5_at(const WorldDev &w, const SunAxes &a
 // too) or once no later column can raise it.  Where the pyramid has a level
 // 5, a round whose region's highest floor (F) or top (G) cannot raise the
 // bound loads no cells; the result is the same.
-__device__ void bounds_of_warp(const WorldDev &w, const SunAxes &a, int32_t cu, int32_t cv,
-                               int32_t NU, int32_t NV, int lane, int32_t &F16, int32_t &G16) {
+__device__ void bounds_of_warp(const WorldDev &w, const SunAxes &a, const int32_t *rq, int32_t cu,
+                               int32_t cv, int32_t NU, int32_t NV, int lane, int32_t &F16,
+                               int32_t &G16) {
     const unsigned full = 0xFFFFFFFFu;
     const int64_t lmaj = a.lmaj, lmin = a.lmin, lz = a.lz;
     const int64_t unit = lmaj << 8;
@@ -137,9 +164,9 @@ __device__ void bounds_of_warp(const WorldDev &w, const SunAxes &a, int32_t cu, 
         const int32_t col = cu + a.smaj * k;
         const bool in_col = col >= 0 && col < NU;
         // rows floor(lmin * j / lmaj) of travel j = k - 1, k, k + 1
-        const int64_t qm = floor_div_est(lmin * (k - 1), lmaj, rcp_maj);
-        const int64_t qk = floor_div_est(lmin * k, lmaj, rcp_maj);
-        const int64_t qp = floor_div_est(lmin * (k + 1), lmaj, rcp_maj);
+        const int64_t qm = rows_after(a, rq, k - 1, rcp_maj);
+        const int64_t qk = rows_after(a, rq, k, rcp_maj);
+        const int64_t qp = rows_after(a, rq, k + 1, rcp_maj);
         const int32_t f0 = cv + (int32_t)min(qm, qk), f1 = cv + 1 + (int32_t)max(qm, qk);
         const int32_t g0 = cv + (int32_t)min(qm, qp), g1 = cv + 1 + (int32_t)max(qm, qp);
         const bool f_ok = in_col && f0 >= 0 && f1 < NV;  // the whole F band in the grid
@@ -194,18 +221,19 @@ __device__ void bounds_of_warp(const WorldDev &w, const SunAxes &a, int32_t cu, 
 // [eu0, eu1) x [ev0, ev1) (major / minor coordinates): some column of the
 // rectangle within `reach` columns downstream, with the cell's widest band
 // over those columns meeting the rectangle's rows.
-__device__ bool depends_on(const SunAxes &a, int32_t cu, int32_t cv, int32_t eu0, int32_t ev0,
-                           int32_t eu1, int32_t ev1, int32_t reach) {
+__device__ bool depends_on(const SunAxes &a, const int32_t *rq, int32_t cu, int32_t cv,
+                           int32_t eu0, int32_t ev0, int32_t eu1, int32_t ev1, int32_t reach) {
     int32_t ka = a.smaj > 0 ? eu0 - cu : cu - (eu1 - 1);
     int32_t kb = a.smaj > 0 ? eu1 - 1 - cu : cu - eu0;
     ka = max(ka, 0);
     kb = min(kb, reach);
     if (ka > kb) return false;
-    const int64_t lmin = a.lmin, lmaj = a.lmaj;
-    const float rcp_maj = 1.0f / (float)lmaj;
-    const int64_t lo = min(lmin * (ka - 1), lmin * (kb + 1)), hi = max(lmin * (ka - 1), lmin * (kb + 1));
-    const int32_t r0 = cv + (int32_t)floor_div_est(lo, lmaj, rcp_maj);
-    const int32_t r1 = cv + 1 + (int32_t)floor_div_est(hi, lmaj, rcp_maj);
+    // floor is monotone, so the band's lowest and highest rows over the
+    // columns ka..kb come from travel ka - 1 and kb + 1
+    const float rcp_maj = 1.0f / (float)a.lmaj;
+    const int64_t qa = rows_after(a, rq, ka - 1, rcp_maj), qb = rows_after(a, rq, kb + 1, rcp_maj);
+    const int32_t r0 = cv + (int32_t)min(qa, qb);
+    const int32_t r1 = cv + 1 + (int32_t)max(qa, qb);
     return r1 >= ev0 && r0 < ev1;
 }
 
@@ -218,16 +246,17 @@ __global__ void k_sun_bounds(const WorldDev w, uint32_t *fg, SunAxes a, int32_t 
     const int lane = threadIdx.x & 31;
     if (i >= n) return;  // warp-uniform
     const int32_t x = x0 + (int32_t)(i % (uint32_t)nx), y = y0 + (int32_t)(i / (uint32_t)nx);
+    const int32_t *rq = reinterpret_cast<const int32_t *>(fg + (size_t)w.W * (size_t)w.H);
     if (edit.z > edit.x) {
-        const bool dep = a.x_major ? depends_on(a, x, y, edit.x, edit.y, edit.z, edit.w, reach)
-                                   : depends_on(a, y, x, edit.y, edit.x, edit.w, edit.z, reach);
+        const bool dep = a.x_major ? depends_on(a, rq, x, y, edit.x, edit.y, edit.z, edit.w, reach)
+                                   : depends_on(a, rq, y, x, edit.y, edit.x, edit.w, edit.z, reach);
         if (!dep) return;  // warp-uniform
     }
     int32_t F16, G16;
     if (a.x_major)
-        bounds_of_warp(w, a, x, y, w.W, w.H, lane, F16, G16);
+        bounds_of_warp(w, a, rq, x, y, w.W, w.H, lane, F16, G16);
     else
-        bounds_of_warp(w, a, y, x, w.H, w.W, lane, F16, G16);
+        bounds_of_warp(w, a, rq, y, x, w.H, w.W, lane, F16, G16);
     if (lane == 0)
         fg[(uint32_t)y * (uint32_t)w.W + (uint32_t)x] =
             (uint32_t)max(F16, 0) | ((uint32_t)max(G16, 0) << 16);
@@ -277,9 +306,19 @@ void sun_bounds_region(const WorldDev &w, const int32_t sun[3], int32_t x0, int3
     out[3] = (int32_t)(a.x_major ? v1 : u1);
 }
 
+size_t sun_bounds_bytes(int32_t W, int32_t H) {
+    return ((size_t)W * (size_t)H + kRowTable) * sizeof(uint32_t);
+}
+
 int sun_bounds(const WorldDev &w, uint32_t *fg, const int32_t sun[3], int32_t x0, int32_t y0,
                int32_t x1, int32_t y1, void *stream) {
     if (!sun_bounds_eligible(sun)) return -1;
+    {  // this sun's row-offset table, which the bounds and later repairs read
+        const SunAxes a = axes_of(sun);
+        k_sun_rows<<<(kRowTable + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
+            reinterpret_cast<int32_t *>(fg + (size_t)w.W * (size_t)w.H), a.lmin, a.lmaj);
+        if (cudaGetLastError() != cudaSuccess) return -1;
+    }
     if (x1 <= x0 || y1 <= y0) return 0;
     const uint32_t nx = (uint32_t)(x1 - x0), n = nx * (uint32_t)(y1 - y0);
     const uint32_t threads = 128, blocks = (n + threads / 32 - 1) / (threads / 32);
