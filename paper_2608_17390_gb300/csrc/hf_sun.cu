@@ -52,22 +52,31 @@
 namespace hf {
 namespace {
 
-constexpr int64_t kS = 1 << kShift;
-
-// Row-offset table after the bounds words: entry j + 1 holds floor(lmin j /
-// lmaj), the minor-axis rows a ray has crossed after j columns of major
-// travel, for j = -1 .. kRowTable - 2.  A bound reads columns up to K + 63
-// (K <= kSunMaxReach), so every lookup is in range; one outside it would
-// fall back to the float-estimated division.
+// Tables after the bounds words, one entry per column of major travel j =
+// -1 .. kRowTable - 2 (entry j + 1), all set by one pass per sun:
+//   rows:  floor(lmin j / lmaj), the minor-axis rows a ray has crossed;
+//   rise:  floor and ceil of 256 j lz / lmaj, its rise in the bounds' units
+//          (2^-8 world units), saturated at kRiseSat (every quantity it is
+//          compared with is below 2^17, so saturation changes no outcome).
+// A bound reads columns up to K + 63 (K <= kSunMaxReach), so every lookup is
+// in range; one outside it would fall back to the float-estimated division.
 constexpr int kRowTable = (int)kSunMaxReach + 128;
+constexpr int32_t kRiseSat = 1 << 21;
 
-__global__ void k_sun_rows(int32_t *q, int64_t lmin, int64_t lmaj) {
+__global__ void k_sun_rows(int32_t *q, int64_t lmin, int64_t lmaj, int64_t lz) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= kRowTable) return;
-    const int64_t a = lmin * (i - 1);
-    int64_t d = a / lmaj;  // once per sun: the exact division is affordable here
-    if (a % lmaj != 0 && a < 0) d -= 1;
-    q[i] = (int32_t)d;
+    // once per sun: exact divisions are affordable here
+    auto floor_div = [](int64_t n, int64_t d) {
+        int64_t f = n / d;
+        if (n % d != 0 && n < 0) f -= 1;
+        return f;
+    };
+    const int64_t j = i - 1, rise = 256 * j * lz;
+    const int64_t fl = floor_div(rise, lmaj), ce = fl + (fl * lmaj != rise ? 1 : 0);
+    q[i] = (int32_t)floor_div(lmin * j, lmaj);
+    q[kRowTable + i] = (int32_t)min(fl, (int64_t)kRiseSat);
+    q[2 * kRowTable + i] = (int32_t)min(ce, (int64_t)kRiseSat);
 }
 
 // Node-form word of level-0 cell (x, y), either storage (top = byte 2, floor = byte 0).
@@ -107,11 +116,22 @@ __device__ __forceinline__ uint32_t node5_at(const WorldDev &w, const SunAxes &a
     return __ldg(w.base + w.off[5] + (uint32_t)y * w.stride[5] + (uint32_t)x);
 }
 
-// floor(lmin * j / lmaj) from the row-offset table.
+// floor(lmin * j / lmaj) from the rows table.
 __device__ __forceinline__ int64_t rows_after(const SunAxes &a, const int32_t *rq, int32_t j,
                                               float rcp_maj) {
     if ((uint32_t)(j + 1) < (uint32_t)kRowTable) return __ldg(rq + j + 1);
     return floor_div_est((int64_t)a.lmin * j, a.lmaj, rcp_maj);
+}
+
+// floor (up = false) or ceil (up = true) of 256 j lz / lmaj, j >= 0,
+// saturated at kRiseSat, from the rise tables.
+__device__ __forceinline__ int32_t rise_after(const SunAxes &a, const int32_t *rq, int32_t j,
+                                              bool up, float rcp_maj) {
+    if ((uint32_t)(j + 1) < (uint32_t)kRowTable) return __ldg(rq + (up ? 2 : 1) * kRowTable + j + 1);
+    const int64_t num = (int64_t)j * 256 * a.lz;
+    if (num >= (int64_t)kRiseSat * a.lmaj) return kRiseSat;
+    const int64_t f = floor_div_est(num, a.lmaj, rcp_maj);
+    return (int32_t)(up && f * a.lmaj != num ? f + 1 : f);
 }
 
 // F and G of the cell at major / minor coordinates (cu, cv), rounded to the
@@ -129,36 +149,33 @@ __device__ void bounds_of_warp(const WorldDev &w, const SunAxes &a, const int32_
                                int32_t cv, int32_t NU, int32_t NV, int lane, int32_t &F16,
                                int32_t &G16) {
     const unsigned full = 0xFFFFFFFFu;
-    const int64_t lmaj = a.lmaj, lmin = a.lmin, lz = a.lz;
-    const int64_t unit = lmaj << 8;
-    const float rcp_maj = 1.0f / (float)lmaj, rcp_unit = 1.0f / (float)unit;
-    const int64_t top_all = 255 * kS * lmaj, rise1 = kS * lz;
-    // rounded terms: negative ones never win (F, G >= 0 from k = 0)
-    auto q_floor = [&](int64_t v) -> int32_t {
-        return v < 0 ? -1 : (int32_t)min(floor_div_est(v, unit, rcp_unit), (int64_t)65535);
-    };
-    auto q_ceil = [&](int64_t v) -> int32_t {
-        return v <= 0 ? 0 : (int32_t)min(-floor_div_est(-v, unit, rcp_unit), (int64_t)65535);
-    };
+    const float rcp_maj = 1.0f / (float)a.lmaj;
+    // In the stored units a term is a height h (a floor for F, a top for G)
+    // times 256, less the rise 256 (k or k - 1) lz / lmaj: exactly, the F term
+    // of column k rounded down is 256 h - ceil(256 k lz / lmaj), and the G term
+    // rounded up is 256 h - floor(256 (k - 1) lz / lmaj).  Negative F terms
+    // and non-positive G terms never win (F, G >= 0 from k = 0).
     const uint32_t c0 = word_at(w, a, cu, cv);
-    F16 = q_floor((int64_t)(c0 & 0xFF) * kS * lmaj);  // k = 0: the start cell's floor
+    F16 = (int32_t)(c0 & 0xFF) << 8;  // k = 0: the start cell's floor
     {  // G, k = 0: the rows the ray can cross in its start column (it moves at
-       // most one row there, |lmin| <= lmaj), strictly above
-        const int32_t r0 = cv + (lmin < 0 ? -1 : 0), r1 = cv + 1;
+       // most one row there, |lmin| <= lmaj), strictly above: top + 2^-16,
+       // rounded up
+        const int32_t r0 = cv + (a.lmin < 0 ? -1 : 0), r1 = cv + 1;
         int32_t t = -1;
         if (lane <= r1 - r0) {
             const int32_t r = r0 + lane;
             if (r >= 0 && r < NV) t = (int32_t)((word_at(w, a, cu, r) >> 16) & 0xFF);
         }
         t = __reduce_max_sync(full, t);
-        G16 = q_ceil(((int64_t)t * kS + 1) * lmaj);
+        G16 = t < 0 ? 0 : (t << 8) + 1;
     }
+    constexpr int32_t top_all = 255 << 8;
     const bool skip = w.L >= 5;
     bool f_on = true, g_on = true;
     for (int32_t k0 = 1;; k0 += 32) {
         // no column from k0 on can raise a bound already this high
-        if (f_on && top_all - (int64_t)k0 * rise1 < (int64_t)(F16 + 1) * unit) f_on = false;
-        if (g_on && top_all - (int64_t)(k0 - 1) * rise1 <= (int64_t)G16 * unit) g_on = false;
+        if (f_on && top_all - (F16 + 1) < rise_after(a, rq, k0, true, rcp_maj)) f_on = false;
+        if (g_on && top_all - G16 <= rise_after(a, rq, k0 - 1, false, rcp_maj)) g_on = false;
         if (!f_on && !g_on) break;
         const int32_t k = k0 + lane;
         const int32_t col = cu + a.smaj * k;
@@ -190,25 +207,31 @@ __device__ void bounds_of_warp(const WorldDev &w, const SunAxes &a, const int32_
                 mh = __reduce_max_sync(full, mh);
                 mt = __reduce_max_sync(full, mt);
             }
-            f_need = f_need && mh >= 0 &&
-                     (int64_t)mh * kS * lmaj - (int64_t)k0 * rise1 >= (int64_t)(F16 + 1) * unit;
-            g_need = g_need && mt >= 0 &&
-                     (int64_t)mt * kS * lmaj - (int64_t)(k0 - 1) * rise1 > (int64_t)G16 * unit;
+            f_need = f_need && mh >= 0 && (mh << 8) - (F16 + 1) >= rise_after(a, rq, k0, true, rcp_maj);
+            g_need = g_need && mt >= 0 && (mt << 8) - G16 > rise_after(a, rq, k0 - 1, false, rcp_maj);
         }
         if (f_need || g_need) {
-            int64_t m = 255, t = -1;
+            int32_t m = 255, t = -1;
             if (g_ok || f_ok)
                 for (int32_t r = max(g0, 0); r <= min(g1, NV - 1); ++r) {
                     const uint32_t c = word_at(w, a, col, r);
-                    if (r >= f0 && r <= f1) m = min(m, (int64_t)(c & 0xFF));
-                    t = max(t, (int64_t)((c >> 16) & 0xFF));
+                    if (r >= f0 && r <= f1) m = min(m, (int32_t)(c & 0xFF));
+                    t = max(t, (int32_t)((c >> 16) & 0xFF));
                 }
             if (f_need) {
-                const int32_t v = f_ok ? q_floor(m * kS * lmaj - (int64_t)k * rise1) : -1;
+                int32_t v = -1;
+                if (f_ok) {
+                    const int32_t q = (m << 8) - rise_after(a, rq, k, true, rcp_maj);
+                    v = q < 0 ? -1 : q;
+                }
                 F16 = max(F16, __reduce_max_sync(full, v));
             }
             if (g_need) {
-                const int32_t v = g_ok ? q_ceil(t * kS * lmaj - (int64_t)(k - 1) * rise1) : 0;
+                int32_t v = 0;
+                if (g_ok) {
+                    const int32_t q = (t << 8) - rise_after(a, rq, k - 1, false, rcp_maj);
+                    v = q <= 0 ? 0 : q;
+                }
                 G16 = max(G16, __reduce_max_sync(full, v));
             }
         }
@@ -307,16 +330,16 @@ void sun_bounds_region(const WorldDev &w, const int32_t sun[3], int32_t x0, int3
 }
 
 size_t sun_bounds_bytes(int32_t W, int32_t H) {
-    return ((size_t)W * (size_t)H + kRowTable) * sizeof(uint32_t);
+    return ((size_t)W * (size_t)H + 3 * (size_t)kRowTable) * sizeof(uint32_t);
 }
 
 int sun_bounds(const WorldDev &w, uint32_t *fg, const int32_t sun[3], int32_t x0, int32_t y0,
                int32_t x1, int32_t y1, void *stream) {
     if (!sun_bounds_eligible(sun)) return -1;
-    {  // this sun's row-offset table, which the bounds and later repairs read
+    {  // this sun's row and rise tables, which the bounds and later repairs read
         const SunAxes a = axes_of(sun);
         k_sun_rows<<<(kRowTable + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
-            reinterpret_cast<int32_t *>(fg + (size_t)w.W * (size_t)w.H), a.lmin, a.lmaj);
+            reinterpret_cast<int32_t *>(fg + (size_t)w.W * (size_t)w.H), a.lmin, a.lmaj, a.lz);
         if (cudaGetLastError() != cudaSuccess) return -1;
     }
     if (x1 <= x0 || y1 <= y0) return 0;
