@@ -39,9 +39,9 @@
 // distance over which a ray rises by 255 units: sun_bounds_region gives the
 // rectangle that holds them, and sun_bounds_repair recomputes, inside it, the
 // cells whose bands reach the edited rectangle (a parallelogram along L).
-// The band rows depend on the column of travel only, not on the cell: a full
-// build first tabulates them (k_sun_rows) after the bounds words, and the
-// build and later repairs read the table instead of dividing.
+// The band rows and the rise depend on the column of travel only, not on the
+// cell: a full build first tabulates them (k_sun_rows) after the bounds words,
+// and the build and later repairs read the tables instead of dividing.
 #include <cuda_runtime.h>
 
 #include <cstdint>
