@@ -265,7 +265,9 @@ __device__ bool depends_on(const SunAxes &a, const int32_t *rq, int32_t cu, int3
 // [edit.x, edit.z) x [edit.y, edit.w) are recomputed (the others keep theirs).
 __global__ void k_sun_bounds(const WorldDev w, uint32_t *fg, SunAxes a, int32_t x0, int32_t y0,
                              int32_t nx, uint32_t n, int4 edit, int32_t reach) {
-    const uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    // the thread index in 64 bits: a warp per cell of a grid of up to 2^28
+    // cells is up to 2^33 threads
+    const uint32_t i = (uint32_t)(((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= n) return;  // warp-uniform
     const int32_t x = x0 + (int32_t)(i % (uint32_t)nx), y = y0 + (int32_t)(i / (uint32_t)nx);

@@ -16,7 +16,9 @@ launch configuration the benchmark times and in the library's default one:
   (640 x 360 to 3840 x 2160) with crater edits every 11th request: each served
   image equals the same request rendered alone on a fresh world holding
   exactly the edits before it, bit for bit, and the oracle on that world
-  (every pixel up to 1920 x 1080, 40,000 sampled pixels per 3840 x 2160 image).
+  (every pixel up to 1920 x 1080, 40,000 sampled pixels per 3840 x 2160 image);
+* the largest grid, 16384 x 16384 (1 GiB of cells), with rays that cross all
+  of it and a camera at the highest allowed altitude.
 
 The paper evaluates its renderers against a CPU ray cast (Section 4.1); here
 the CPU ray cast is the oracle and the bar is exact.
@@ -189,3 +191,44 @@ def test_c5_serving_on_the_large_world(hf):
             world[y0:y0 + blk.shape[0], x0:x0 + blk.shape[1]] = blk
         k = j + 1
     assert checked == 40
+
+
+def _max_world(seed=11):
+    """A 16384 x 16384 world (the largest grid, 1 GiB of cells): 64-cell
+    blocks of random height with per-cell noise, a few 200-high ridges, and
+    slabs over about a tenth of the cells."""
+    n = int(16384)
+    rng = np.random.default_rng(seed)
+    h0 = np.repeat(np.repeat(rng.integers(0, 120, (n // 64, n // 64), dtype=np.uint8), 64, 0), 64, 1)
+    h0 += rng.integers(0, 8, (n, n), dtype=np.uint8)
+    h0[4096::4096, :] = 200
+    h0[:, 6000] = 200
+    slab = (rng.integers(0, 10, (n, n), dtype=np.uint8) == 0) & (h0 < 200)
+    h1 = np.where(slab, h0 + 10, 0).astype(np.uint8)
+    h2 = np.where(slab, h1 + 6, 0).astype(np.uint8)
+    return synth.pack_cells(h0, h1, h2, h0 & 7)
+
+
+def test_largest_grid_and_camera_extremes(hf):
+    """The largest grid (16384 x 16384) with shadow rays: rays that cross the
+    whole world and leave it at the far corner, a camera at the highest
+    allowed altitude (z just under 2^28 fixed-point units) looking straight
+    down over 14,000 cells, and one in the far corner looking back; every
+    pixel equals the oracle, and the batched and plain launches agree."""
+    cells = _max_world()
+    cams = synth.camera_array([
+        synth.pose_to_camera(0.5, 0.5, 150.0, 45, -0.06, 20, 48, 12),
+        synth.pose_to_camera(8192.5, 8192.5, 4095.0, 0, -90, 120, 64, 64),
+        synth.pose_to_camera(16383.5, 16383.5, 140.0, 225, 0.5, 90, 33, 9)])
+    ctx = hf.hf_create(cells)
+    try:
+        opts = hf.make_opts(flags=hf.HF_SHADOWS)
+        g = _render(hf, ctx, cams, True, opts)
+        p = _render(hf, ctx, cams, True, hf.make_opts(flags=hf.HF_SHADOWS | hf.HF_PLAIN))
+        for i in range(len(cams)):
+            _assert_identical(g[i], p[i], "camera %d batched vs plain" % i)
+        for i, c in enumerate(cams):
+            compare(_host(g[i]), oracle.render(cells, c, shadows=True, nthreads=NT), shadows=True,
+                    what="largest grid, camera %d" % i)
+    finally:
+        hf.hf_destroy(ctx)
