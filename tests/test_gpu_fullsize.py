@@ -18,7 +18,8 @@ launch configuration the benchmark times and in the library's default one:
   exactly the edits before it, bit for bit, and the oracle on that world
   (every pixel up to 1920 x 1080, 40,000 sampled pixels per 3840 x 2160 image);
 * the largest grid, 16384 x 16384 (1 GiB of cells), with rays that cross all
-  of it and a camera at the highest allowed altitude.
+  of it and a camera at the highest allowed altitude;
+* the largest batch (4096 cameras) and the largest image (16384 x 16384).
 
 The paper evaluates its renderers against a CPU ray cast (Section 4.1); here
 the CPU ray cast is the oracle and the bar is exact.
@@ -230,5 +231,51 @@ def test_largest_grid_and_camera_extremes(hf):
         for i, c in enumerate(cams):
             compare(_host(g[i]), oracle.render(cells, c, shadows=True, nthreads=NT), shadows=True,
                     what="largest grid, camera %d" % i)
+    finally:
+        hf.hf_destroy(ctx)
+
+
+def test_largest_batch_and_largest_image(hf):
+    """The batch limit and the image limit, with shadow rays: HF_MAX_CAMERAS
+    (4096) small cameras in one batched launch equal the plain launches and
+    the oracle, one camera more is refused; a 16384 x 16384 image (268 M
+    primary rays) is identical from the plain and the batched kernel and
+    equals the oracle on 100,000 sampled pixels."""
+    import torch
+
+    cells = synth.config_c1()["cells"]
+    rng = np.random.default_rng(3)
+    n = int(hf.HF_MAX_CAMERAS)
+    poses = [synth.pose_to_camera(float(rng.uniform(1, 255)), float(rng.uniform(1, 255)),
+                                  float(rng.uniform(20, 250)), float(rng.uniform(0, 360)),
+                                  float(rng.uniform(-89, 10)), float(rng.uniform(40, 100)), 8, 4)
+             for _ in range(n + 1)]
+    cams = synth.camera_array(poses)
+    ctx = hf.hf_create(cells)
+    try:
+        with pytest.raises(hf.HFError) as e:
+            hf.hf_render(ctx, cams, hf.alloc_outputs(cams, shadows=True),
+                         hf.make_opts(flags=hf.HF_SHADOWS))
+        assert e.value.code == hf.HF_E_INVALID_ARG
+        cams = cams[:n]
+        g = _render(hf, ctx, cams, True, hf.make_opts(flags=hf.HF_SHADOWS))
+        p = _render(hf, ctx, cams, True, hf.make_opts(flags=hf.HF_SHADOWS | hf.HF_PLAIN))
+        for i in range(n):
+            _assert_identical(g[i], p[i], "camera %d of the largest batch" % i)
+        for i in range(0, n, 97):
+            compare(_host(g[i]), oracle.render(cells, cams[i], shadows=True), shadows=True,
+                    what="largest batch, camera %d" % i)
+
+        big = synth.camera_array([synth.pose_to_camera(128.5, 128.5, 200.0, 30, -60, 100,
+                                                       16384, 16384)])
+        a = _render(hf, ctx, big, True, hf.make_opts(flags=hf.HF_SHADOWS))
+        b = _render(hf, ctx, big, True, hf.make_opts(flags=hf.HF_SHADOWS | hf.HF_NOGRAPH))
+        _assert_identical(a[0], b[0], "largest image, plain vs batched")
+        del b
+        pix = sample_pixels(16384, 16384, 100000, 17)
+        compare(_host(a[0], pix), oracle.render(cells, big[0], shadows=True, pix=pix, nthreads=NT),
+                shadows=True, what="largest image")
+        del a
+        torch.cuda.empty_cache()
     finally:
         hf.hf_destroy(ctx)
