@@ -18,7 +18,8 @@ launch configuration the benchmark times and in the library's default one:
   exactly the edits before it, bit for bit, and the oracle on that world
   (every pixel up to 1920 x 1080, 40,000 sampled pixels per 3840 x 2160 image);
 * the largest grid, 16384 x 16384 (1 GiB of cells), with rays that cross all
-  of it and a camera at the highest allowed altitude;
+  of it and a camera at the highest allowed altitude, and its pyramid and
+  shadow bounds after large edits against a fresh build;
 * the largest batch (4096 cameras) and the largest image (16384 x 16384).
 
 The paper evaluates its renderers against a CPU ray cast (Section 4.1); here
@@ -279,3 +280,44 @@ def test_largest_batch_and_largest_image(hf):
         torch.cuda.empty_cache()
     finally:
         hf.hf_destroy(ctx)
+
+
+def test_largest_grid_edits_repair_pyramid_and_bounds(hf):
+    """Edits on the largest grid after a shadowed render: a full-width strip
+    across the 2^27-cell index (rows 8180-8219) and a crater in the far
+    corner.  The repaired pyramid levels and shadow bounds equal a fresh
+    world's bit for bit, and the renders equal the oracle on the edited cells."""
+    cells = _max_world(seed=12)
+    cams = synth.camera_array([
+        synth.pose_to_camera(8192.5, 8150.5, 300.0, 0, -20, 90, 64, 32),
+        synth.pose_to_camera(16300.5, 16250.5, 120.0, 30, -30, 90, 48, 24)])
+    rng = np.random.default_rng(13)
+    strip = synth.pack_cells(rng.integers(0, 150, (40, 16384)), 0, 0, rng.integers(0, 8, (40, 16384)))
+    ctx = hf.hf_create(cells)
+    fresh = None
+    try:
+        opts = hf.make_opts(flags=hf.HF_SHADOWS)
+        _render(hf, ctx, cams, True, opts)  # builds the shadow bounds
+        hf.hf_edit(ctx, 0, 8180, strip)
+        cells[8180:8220, :] = strip
+        x0, y0, blk = synth.crater_edit(cells, 16330, 16340)
+        hf.hf_edit(ctx, x0, y0, blk)
+        cells[y0:y0 + blk.shape[0], x0:x0 + blk.shape[1]] = blk
+        g = _render(hf, ctx, cams, True, opts)
+        hf.hf_sync(ctx)
+        fresh = hf.hf_create(cells)
+        _render(hf, fresh, cams, True, opts)
+        hf.hf_sync(fresh)
+        for level in (1, 2, 5, 9, 14):
+            assert np.array_equal(hf.hf_read_pyramid(ctx, level), hf.hf_read_pyramid(fresh, level)), \
+                "pyramid level %d after edits differs from a fresh build" % level
+        got, s1 = hf.hf_read_sun_bounds(ctx)
+        want, s2 = hf.hf_read_sun_bounds(fresh)
+        assert s1 == s2 and np.array_equal(got, want), "repaired shadow bounds differ from a fresh build"
+        for i, c in enumerate(cams):
+            compare(_host(g[i]), oracle.render(cells, c, shadows=True, nthreads=NT), shadows=True,
+                    what="largest grid after edits, camera %d" % i)
+    finally:
+        hf.hf_destroy(ctx)
+        if fresh is not None:
+            hf.hf_destroy(fresh)
